@@ -1,0 +1,92 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle.
+
+Holds no arithmetic of the emulation method: only random draws and the matrix
+families of arXiv 2509.23565.  Every generator returns float64 numpy arrays in
+column-major (Fortran) order, the layout of the C-ABI.
+
+* uniform(m, n, seed, lo, hi)      iid U(lo, hi) entries (HPL draws U(-1/2, 1/2),
+                                   Section 6; the dynamic-range sweeps use U(-1, 1)).
+* log_scaled(m, n, r, seed)        u * 10**e, u ~ U(-1, 1), e ~ U(-r, r) continuous.
+* spd(n, cond, seed)               Q diag(lam) Q^T, Q from the QR of a Gaussian
+                                   matrix, lam log-spaced from 1 to 1/cond.
+* wilkinson(n)                     Eq. 9 (diagonal 1, -1 below, 1 in the last column).
+* turing(n)                        the matrix of Eq. 10 (no last-column 1's).
+* parawilk(n, d, b, alpha)         Section 5: d subdiagonals of -1, alpha above the
+                                   diagonal in every b-th column (1-based j = 1+b, 1+2b, ...)
+                                   and in the last column (Eq. 11, 13).
+* parawilk_random(n, d, b, alpha, seed)
+                                   Eq. 15: 2 u**2 (u ~ U(0, 1)) in the zero
+                                   positions of parawilk, parawilk elsewhere.
+"""
+import numpy as np
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+def uniform(m, n, seed, lo=-1.0, hi=1.0):
+    rng = _rng(seed)
+    x = rng.random((n, m))                        # generated column by column
+    x *= (hi - lo)
+    x += lo
+    return np.asfortranarray(x.T)
+
+
+def log_scaled(m, n, r, seed):
+    rng = _rng(seed)
+    u = rng.random((n, m)) * 2.0 - 1.0
+    u[u == 0.0] = 0.5
+    e = (rng.random((n, m)) * 2.0 - 1.0) * r
+    return np.asfortranarray((u * np.power(10.0, e)).T)
+
+
+def vector(n, seed, lo=-1.0, hi=1.0):
+    rng = _rng(seed)
+    return rng.random(n) * (hi - lo) + lo
+
+
+def spd(n, cond, seed):
+    rng = _rng(seed)
+    G = rng.standard_normal((n, n))
+    Q, R = np.linalg.qr(G)
+    Q = Q * np.sign(np.diag(R))[None, :]
+    lam = np.logspace(0.0, -np.log10(cond), n)
+    A = (Q * lam[None, :]) @ Q.T
+    A = 0.5 * (A + A.T)
+    return np.asfortranarray(A)
+
+
+def turing(n):
+    A = np.eye(n) - np.tril(np.ones((n, n)), -1)
+    return np.asfortranarray(A)
+
+
+def wilkinson(n):
+    A = turing(n)
+    A[:, n - 1] = 1.0
+    return np.asfortranarray(A)
+
+
+def parawilk(n, d, b, alpha):
+    A = np.eye(n)
+    for k in range(1, min(d, n - 1) + 1):
+        A -= np.eye(n, k=-k)
+    cols = [j for j in range(1, n) if j % b == 0] + [n - 1]   # 0-based: 1-based j = 1+b, 1+2b, ..., n
+    for j in set(cols):
+        A[:j, j] = alpha
+    return np.asfortranarray(A)
+
+
+def parawilk_random(n, d, b, alpha, seed):
+    P = parawilk(n, d, b, alpha)
+    rng = _rng(seed)
+    u = rng.random((n, n)).T
+    fill = 2.0 * u * u
+    return np.asfortranarray(np.where(P == 0.0, fill, P))
+
+
+def batch_sizes(count, lo, hi, seed):
+    """Log-uniform integer sizes in [lo, hi] for the batched solver."""
+    rng = _rng(seed)
+    return np.floor(np.exp(rng.uniform(np.log(lo), np.log(hi + 1), count))).astype(np.int64).clip(lo, hi)

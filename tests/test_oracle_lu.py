@@ -1,0 +1,158 @@
+"""Pins of the oracle's factorizations and solves (Section 4-7, Eq. 5-15).
+
+* FP64 blocked LU against LAPACK (scipy.linalg.lu_factor): same pivots, same factors.
+* Wilkinson growth (Section 5): max |U| = 2**(n-1) under partial pivoting.
+* The worked inverses of Eq. 10, 11 and 13 (golden fixtures).
+* Cholesky against LAPACK (numpy.linalg.cholesky).
+* Scaled residual of Eq. 8 below 16 for FP64 and for s = 8 emulation; far above
+  16 for s = 3; Table 1's per-split trend on ParaWilk_256(4, 15, 1/2).
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import lu, residual
+from paper_2509_23565_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            rows.append([Fraction(tok) for tok in line.split()])
+    return rows
+
+
+@pytest.mark.parametrize("n,nb", [(200, 32), (97, 16), (64, 64), (5, 2)])
+def test_getrf_fp64_matches_lapack(n, nb):
+    A = inputs.uniform(n, n, seed=100 + n)
+    LU, ipiv, info = lu.getrf(A, nb=nb)
+    lu_ref, piv_ref = scipy.linalg.lu_factor(A)
+    assert info == 0
+    assert (ipiv == piv_ref + 1).all()
+    assert np.abs(LU - lu_ref).max() < 1e-10
+    assert residual.lu_residual(A, LU, ipiv) < 1.0
+
+
+@pytest.mark.parametrize("n", [8, 16, 32, 60])
+def test_wilkinson_growth(n):
+    LU, ipiv, info = lu.getrf(inputs.wilkinson(n), nb=8)
+    assert info == 0
+    assert (ipiv == np.arange(1, n + 1)).all()
+    assert np.abs(np.triu(LU)).max() == 2.0 ** (n - 1)
+
+
+@pytest.mark.parametrize("name,A", [
+    ("eq10_turing_inverse.txt", inputs.turing(5)),
+    ("eq11_fibonacci_inverse.txt", inputs.parawilk(5, 2, 2, 0.0)),
+    ("eq13_blocked_inverse.txt", inputs.parawilk(5, 5, 2, 1.0)),
+])
+def test_worked_inverses(name, A):
+    want = np.array([[float(x) for x in row] for row in _load_golden(name)])
+    LU, ipiv, info = lu.getrf(A, nb=2)
+    assert info == 0
+    inv = lu.getrs(LU, ipiv, np.eye(5))
+    assert np.abs(inv - want).max() <= 1e-15
+
+
+def test_singular_matrix_info():
+    A = inputs.uniform(6, 6, seed=7)
+    A[:, 3] = 0.0
+    _, _, info = lu.getrf(A, nb=2)
+    assert info == 4
+
+
+@pytest.mark.parametrize("n,nb", [(150, 32), (64, 16)])
+def test_potrf_matches_lapack(n, nb):
+    A = inputs.spd(n, 1e6, seed=200 + n)
+    L, info = lu.potrf(A, nb=nb)
+    assert info == 0
+    assert np.abs(L - np.linalg.cholesky(A)).max() < 1e-10
+    assert residual.chol_residual(A, L) < 1.0
+    b = inputs.vector(n, seed=9)
+    x = lu.potrs(L, b)
+    assert residual.backward_error(A, x, b) < 16
+
+
+def test_potrf_not_spd_info():
+    A = inputs.spd(20, 10.0, seed=3)
+    A[7, 7] = -1.0
+    _, info = lu.potrf(A, nb=4)
+    assert info == 8
+
+
+def test_fp64_solve_backward_error():
+    n = 300
+    A = inputs.uniform(n, n, seed=301)
+    b = inputs.vector(n, seed=302)
+    LU, ipiv, _ = lu.getrf(A, nb=64)
+    x = lu.getrs(LU, ipiv, b)
+    assert residual.scaled_residual(A, x, b) < 16
+    assert residual.backward_error(A, x, b) < 16
+    # closed form: x with a known solution
+    xs = np.arange(1.0, n + 1.0)
+    x2 = lu.getrs(LU, ipiv, A @ xs)
+    assert np.abs(x2 - xs).max() / n < 1e-10
+
+
+def test_emulated_lu_passes_at_8_and_fails_at_3():
+    n = 192
+    A = inputs.uniform(n, n, seed=401)
+    b = inputs.vector(n, seed=402)
+    res = {}
+    for s in (3, 8):
+        LU, ipiv, info = lu.getrf(A, nb=64, update="emulated", s=s)
+        x = lu.getrs(LU, ipiv, b)
+        res[s] = residual.backward_error(A, x, b)
+    assert res[8] < 16
+    assert res[3] > 16
+
+
+def test_emulated_cholesky_passes_at_8():
+    n = 160
+    A = inputs.spd(n, 1e4, seed=501)
+    b = inputs.vector(n, seed=502)
+    L, info = lu.potrf(A, nb=64, update="emulated", s=8)
+    assert info == 0
+    x = lu.potrs(L, b)
+    assert residual.backward_error(A, x, b) < 16
+
+
+@pytest.mark.slow
+def test_table1_trend_parawilk256():
+    """Table 1: on ParaWilk_256(4, 15, 1/2) the scaled residual falls about two
+    orders of magnitude per added split, 6 splits fail and 7 pass.  The exact
+    values depend on the paper's library, blocking and generator draw, so the
+    pin is the boundary, the monotone trend and a factor-4 band per split."""
+    rows = {}
+    with open(os.path.join(GOLDEN, "table1_parawilk256.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                rows[k] = float(v)
+    n = 256
+    A = inputs.parawilk_random(n, 4, 15, 0.5, seed=256)
+    b = inputs.vector(n, seed=257)
+    LU, ipiv, _ = lu.getrf(A, nb=64)
+    fp64 = residual.scaled_residual(A, lu.getrs(LU, ipiv, b), b)
+    assert fp64 < 16 and 1e-3 * rows["fp64"] < fp64 < 1e3 * rows["fp64"]
+    res = []
+    for s in (3, 4, 5, 6, 7, 8):
+        LU, ipiv, _ = lu.getrf(A, nb=64, update="emulated", s=s)
+        res.append(residual.scaled_residual(A, lu.getrs(LU, ipiv, b), b))
+    paper = [rows[str(s)] for s in (3, 4, 5, 6, 7, 8)]
+    assert all(res[i] > res[i + 1] for i in range(len(res) - 1)), res
+    # the pass/fail boundary of Table 1: 6 splits fail the bar of 16, 7 pass
+    assert res[3] > 16 and res[4] < 16, res
+    # every value within a factor 4 of the printed one (same generator family,
+    # different draw and library)
+    for got, want in zip(res, paper):
+        assert want / 4 < got < want * 4, (res, paper)
