@@ -1,0 +1,145 @@
+/*
+ * emul.h -- C ABI of the GB300 (sm_103a) library for FP64 matrix products
+ * emulated by split-integer arithmetic, used as the trailing-matrix update of
+ * blocked LU (partial pivoting) and Cholesky factorizations.
+ *
+ * Method: arXiv 2509.23565, "Performance and Numerical Aspects of
+ * Decompositional Factorizations with FP64 Floating-Point Emulation in INT8".
+ *   Section 2, Eq. 1-2: split each FP64 operand into s INT8 pieces and sum the
+ *     piece products, dropping those with i+j > t (threshold t = s+1 here).
+ *   Section 2, Eq. 3-4: split pieces carry no exponent; each row of A and each
+ *     column of B gets its own power-of-two scale.
+ *   Section 4, Eq. 5-7: blocked LU; all third-order work is the Schur
+ *     complement A22 <- A22 - L21 U12, computed by the emulated product.
+ *   Section 4, Eq. 8: scaled residual, below 16 for a valid solve.
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are column-major (LAPACK) with a leading dimension ld >= rows.
+ *   - Matrix / vector pointers are DEVICE pointers owned by the caller.  The
+ *     library owns only its workspace, held by the handle.
+ *   - Work is enqueued on the handle's stream; calls return before the GPU is
+ *     done unless stated.  Device faults surface at the caller's next sync.
+ *   - ipiv is 1-based int32 on the device (LAPACK semantics).  info is int32
+ *     on the device: 0 = success, k > 0 = zero pivot / non-SPD leading minor
+ *     at 1-based index k.
+ *   - `slices` is s, the number of signed 7-bit INT8 slices per operand
+ *     (3..8).  The slice products run on tcgen05 tensor cores as integer-valued
+ *     BF16 with FP32 accumulation that is kept exact (|partial sums| < 2^24).
+ *   - Return value: EMUL_OK or a negative status below.  On an error,
+ *     emul_last_error(h) gives a one-line reason.  Nothing is enqueued when
+ *     argument checking fails.
+ */
+#ifndef EMUL_H_
+#define EMUL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EMUL_OK 0
+#define EMUL_INVALID_ARG (-1)    /* a size, pointer, ld or slice count is invalid */
+#define EMUL_CUDA_ERROR (-2)     /* a CUDA runtime / driver call failed */
+#define EMUL_NO_WORKSPACE (-3)   /* the workspace could not be allocated */
+#define EMUL_TIMEOUT (-4)        /* a device-side wait gave up (kernel returned early) */
+#define EMUL_NOT_SUPPORTED (-5)  /* this GPU / configuration is not supported */
+
+typedef struct emul_handle_s* emul_handle_t;
+
+/* Create a handle bound to `stream` (a cudaStream_t; NULL = the legacy default
+ * stream) on the current device.  Requires compute capability 10.3. */
+int emul_create(emul_handle_t* handle, void* stream);
+/* Free the handle and its workspace (synchronises its stream first). */
+int emul_destroy(emul_handle_t handle);
+/* Re-bind the handle to another cudaStream_t. */
+int emul_set_stream(emul_handle_t handle, void* stream);
+/* One-line description of the last error on this handle ("" if none). */
+const char* emul_last_error(emul_handle_t handle);
+/* Synchronise the handle's stream and read the device status word: EMUL_OK,
+ * or EMUL_TIMEOUT if any kernel since the last call gave up on a wait.  Clears it. */
+int emul_sync_status(emul_handle_t handle);
+/* Bytes of device workspace currently held by the handle. */
+size_t emul_workspace_bytes(emul_handle_t handle);
+
+/* ---------------------------------------------------------------- steps --
+ * Exposed individually so each step of the method can be checked bit for bit.
+ */
+
+/* Scale extraction and slicing of a GEMM operand (Section 2, Eq. 1-4).
+ * The operand is `rows` x `k`: element (r, c) at X[r*rs + c*cs] with either
+ * rs == 1 (rows contiguous, e.g. A in column-major: rs=1, cs=lda) or cs == 1
+ * (k contiguous, e.g. the columns of B: rs=ldb, cs=1).
+ *   exps[r] (int32, device): smallest e with max_c |x(r,c)| < 2^e; 0 for an
+ *     all-zero row; 2147483647 if the row holds Inf or NaN.
+ *   slices (device, bf16 bit patterns): plane p (0-based, most significant
+ *     first) at slices[(p*rows + r)*ldk + c] holds the integer
+ *     sign(x) * ((|N| >> 7(s-1-p)) & 127) with N = trunc(x * 2^(7s - e_r)).
+ *   ldk >= k and ldk % 8 == 0.
+ */
+int emul_split(emul_handle_t h, int rows, int k, const double* X, long rs, long cs, int slices, int32_t* exps,
+               uint16_t* slice_out, long ldk);
+
+/* Level sums of the slice-pair products (Section 2, Eq. 2 with t = s+1):
+ *   levels[(L-2)*ldl_plane + i + j*ldl] = sum_{p+q=L} sum_k SA_p(i,k) SB_q(j,k)
+ * for L = 2..s+1, as exact int32, computed on the tensor cores from the slices
+ * of A (m x k, lda) by rows and of B (k x n, ldb) by columns. */
+int emul_level_sums(emul_handle_t h, int m, int n, int k, const double* A, int lda, const double* B, int ldb,
+                    int slices, int32_t* levels, int ldl, long ldl_plane);
+
+/* ---------------------------------------------------------------- BLAS --
+ * C <- beta*C + alpha*(A B), A m x k (lda), B k x n (ldb), C m x n (ldc).
+ * The kept slice-pair products are summed exactly and rounded once to FP64,
+ * D = RN(sum), then C = RN(RN(alpha*D) + RN(beta*C)) (beta == 0: C is not read).
+ * For alpha = -1, beta = 1 this is the Schur update of Eq. 7, C = RN(C - D).
+ */
+int emul_dgemm(emul_handle_t h, int m, int n, int k, double alpha, const double* A, int lda, const double* B,
+               int ldb, double beta, double* C, int ldc, int slices);
+
+/* ------------------------------------------------------- factorizations --
+ * Optional statistics of a factorization call (host memory, may be NULL).
+ */
+typedef struct emul_stats {
+  int steps;          /* block steps taken */
+  int slices_min;     /* smallest slice count used by a trailing update */
+  int slices_max;     /* largest slice count used by a trailing update */
+  int checks_failed;  /* a-posteriori checks that triggered a recomputation */
+  double seconds;     /* host wall time of the call (set only when it synchronises) */
+} emul_stats;
+
+/* LU with partial pivoting of the n x n matrix A (lda), in place (Section 4,
+ * Eq. 5-7): right-looking, block size nb (64..256, multiple of 16; 0 = default
+ * 128).  The panel is factored in FP64 (pivot search, swaps, scaling); the
+ * triangular solve for U12 and the trailing update use the emulated product
+ * with `slices` slices.  ipiv: n int32 (device); info: 1 int32 (device). */
+int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int nb, int slices, int32_t* info,
+                emul_stats* stats);
+
+/* Solve A X = B with the factors from emul_dgetrf: B (n x nrhs, ldb) is
+ * overwritten by X.  FP64 substitution. */
+int emul_dgetrs(emul_handle_t h, int n, int nrhs, const double* LU, int lda, const int32_t* ipiv, double* B,
+                int ldb);
+
+/* Lower Cholesky A = L L^T of the symmetric positive definite n x n matrix A
+ * (lda), in place; only the lower triangle is read and written.  Diagonal
+ * blocks in FP64; L21 = A21 L11^-T and the trailing update (lower tiles only)
+ * use the emulated product.  uplo must be 'L'. */
+int emul_dpotrf(emul_handle_t h, char uplo, int n, double* A, int lda, int nb, int slices, int32_t* info,
+                emul_stats* stats);
+
+/* Solve A X = B from emul_dpotrf's factor (B n x nrhs, overwritten). */
+int emul_dpotrs(emul_handle_t h, char uplo, int n, int nrhs, const double* L, int lda, double* B, int ldb);
+
+/* Residual measures of the solve (Section 4, Eq. 8), computed in FP64 on the
+ * device.  out (device, 2 doubles):
+ *   out[0] = ||Ax-b||_inf / ((||A||_inf ||x||_inf + ||b||_inf) n eps)   (Eq. 8)
+ *   out[1] = ||Ax-b||_inf / (||A||_inf ||x||_inf n eps)
+ * with eps = 2^-53. */
+int emul_backward_error(emul_handle_t h, int n, const double* A, int lda, const double* x, const double* b,
+                        double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EMUL_H_ */

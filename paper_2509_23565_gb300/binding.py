@@ -1,0 +1,210 @@
+"""Thin ctypes binding of the C-ABI library (include/emul.h).
+
+Argument marshalling only: every step runs inside libemul.so.  Loading fails
+loudly if the library has not been built (there is no fallback).  PyTorch is
+used for device memory and streams.
+
+Matrices cross the boundary in column-major order.  A column-major m x n matrix
+with leading dimension ld is held here as a torch tensor `store` of shape
+(n, ld) (row j of `store` is column j of the matrix); ``ColMajor`` wraps it.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libemul.so")
+
+EMUL_OK = 0
+STATUS = {0: "EMUL_OK", -1: "EMUL_INVALID_ARG", -2: "EMUL_CUDA_ERROR", -3: "EMUL_NO_WORKSPACE",
+          -4: "EMUL_TIMEOUT", -5: "EMUL_NOT_SUPPORTED"}
+
+# name -> (restype, argtypes); mirrors include/emul.h
+_c_int, _c_long, _c_double, _vp, _c_char = ctypes.c_int, ctypes.c_long, ctypes.c_double, ctypes.c_void_p, ctypes.c_char
+SIGNATURES = {
+    "emul_create": (_c_int, [ctypes.POINTER(_vp), _vp]),
+    "emul_destroy": (_c_int, [_vp]),
+    "emul_set_stream": (_c_int, [_vp, _vp]),
+    "emul_last_error": (ctypes.c_char_p, [_vp]),
+    "emul_sync_status": (_c_int, [_vp]),
+    "emul_workspace_bytes": (ctypes.c_size_t, [_vp]),
+    "emul_split": (_c_int, [_vp, _c_int, _c_int, _vp, _c_long, _c_long, _c_int, _vp, _vp, _c_long]),
+    "emul_level_sums": (_c_int, [_vp, _c_int, _c_int, _c_int, _vp, _c_int, _vp, _c_int, _c_int, _vp, _c_int,
+                                 _c_long]),
+    "emul_dgemm": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_double, _vp, _c_int, _vp, _c_int, _c_double, _vp,
+                            _c_int, _c_int]),
+    "emul_dgetrf": (_c_int, [_vp, _c_int, _vp, _c_int, _vp, _c_int, _c_int, _vp, _vp]),
+    "emul_dgetrs": (_c_int, [_vp, _c_int, _c_int, _vp, _c_int, _vp, _vp, _c_int]),
+    "emul_dpotrf": (_c_int, [_vp, _c_char, _c_int, _vp, _c_int, _c_int, _c_int, _vp, _vp]),
+    "emul_dpotrs": (_c_int, [_vp, _c_char, _c_int, _c_int, _vp, _c_int, _vp, _c_int]),
+    "emul_backward_error": (_c_int, [_vp, _c_int, _vp, _c_int, _vp, _vp, _vp]),
+}
+
+_LIB = None
+
+
+class EmulError(RuntimeError):
+    pass
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("slices_min", ctypes.c_int), ("slices_max", ctypes.c_int),
+                ("checks_failed", ctypes.c_int), ("seconds", ctypes.c_double)]
+
+
+def load():
+    """Load libemul.so and declare every exported signature (no CUDA call)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise EmulError(f"{LIB_PATH} is missing: run __graft_entry__.build() first")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+class ColMajor:
+    """Column-major m x n FP64 (or other dtype) matrix on the device."""
+
+    def __init__(self, store, m, n):
+        self.store, self.m, self.n = store, m, n
+        self.ld = store.shape[1]
+
+    @property
+    def ptr(self):
+        return self.store.data_ptr()
+
+    @staticmethod
+    def from_numpy(A, device="cuda", ld=None, dtype=None):
+        import torch
+        A = np.asarray(A)
+        if A.ndim == 1:
+            A = A[:, None]
+        m, n = A.shape
+        ld = m if ld is None else ld
+        buf = np.zeros((n, max(ld, 1)), dtype=A.dtype if dtype is None else dtype)
+        buf[:, :m] = A.T
+        return ColMajor(torch.from_numpy(buf).to(device), m, n)
+
+    @staticmethod
+    def empty(m, n, device="cuda", ld=None, dtype=None):
+        import torch
+        ld = m if ld is None else ld
+        return ColMajor(torch.zeros((n, max(ld, 1)), dtype=dtype or torch.float64, device=device), m, n)
+
+    def numpy(self):
+        return self.store[:, :self.m].cpu().numpy().T.copy()
+
+
+class Emul:
+    """One library handle bound to a CUDA stream (default: torch's current stream)."""
+
+    def __init__(self, stream=None):
+        import torch
+        self.lib = load()
+        self.h = _vp()
+        st = (stream or torch.cuda.current_stream()).cuda_stream
+        self._check(self.lib.emul_create(ctypes.byref(self.h), _vp(st)), "emul_create")
+
+    def close(self):
+        if self.h:
+            self.lib.emul_destroy(self.h)
+            self.h = _vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != EMUL_OK:
+            msg = self.lib.emul_last_error(self.h).decode() if self.h else ""
+            raise EmulError(f"{what}: {STATUS.get(rc, rc)} {msg}")
+
+    def set_stream(self, stream):
+        self._check(self.lib.emul_set_stream(self.h, _vp(stream.cuda_stream)), "emul_set_stream")
+
+    def sync_status(self):
+        self._check(self.lib.emul_sync_status(self.h), "emul_sync_status")
+
+    def workspace_bytes(self):
+        return int(self.lib.emul_workspace_bytes(self.h))
+
+    # ---------------------------------------------------------------- steps
+    def split(self, X, slices, by="rows"):
+        """Slices of a ColMajor operand by rows (A) or by columns (B).
+        Returns (exps int32 [rows], slices int16 view of BF16 bits [s, rows, ldk])."""
+        import torch
+        if by == "rows":
+            rows, k, rs, cs = X.m, X.n, 1, X.ld
+        else:
+            rows, k, rs, cs = X.n, X.m, X.ld, 1
+        ldk = (k + 7) // 8 * 8
+        exps = torch.zeros(max(rows, 1), dtype=torch.int32, device="cuda")
+        out = torch.zeros((slices, max(rows, 1), max(ldk, 8)), dtype=torch.int16, device="cuda")
+        self._check(self.lib.emul_split(self.h, rows, k, _vp(X.ptr), rs, cs, slices, _vp(exps.data_ptr()),
+                                        _vp(out.data_ptr()), max(ldk, 8)), "emul_split")
+        return exps[:rows], out[:, :rows, :k]
+
+    def level_sums(self, A, B, slices):
+        import torch
+        m, k, n = A.m, A.n, B.n
+        out = torch.zeros((slices, n, max(m, 1)), dtype=torch.int32, device="cuda")
+        self._check(self.lib.emul_level_sums(self.h, m, n, k, _vp(A.ptr), A.ld, _vp(B.ptr), B.ld, slices,
+                                             _vp(out.data_ptr()), max(m, 1), n * max(m, 1)), "emul_level_sums")
+        return out   # out[L-2, j, i] = I_L(i, j)
+
+    # ---------------------------------------------------------------- BLAS / LAPACK
+    def dgemm(self, A, B, C, slices, alpha=1.0, beta=0.0):
+        self._check(self.lib.emul_dgemm(self.h, C.m, C.n, A.n, alpha, _vp(A.ptr), A.ld, _vp(B.ptr), B.ld, beta,
+                                        _vp(C.ptr), C.ld, slices), "emul_dgemm")
+
+    def dgetrf(self, A, nb=0, slices=7, stats=False):
+        import torch
+        ipiv = torch.zeros(max(A.m, 1), dtype=torch.int32, device="cuda")
+        info = torch.zeros(1, dtype=torch.int32, device="cuda")
+        st = Stats()
+        self._check(self.lib.emul_dgetrf(self.h, A.m, _vp(A.ptr), A.ld, _vp(ipiv.data_ptr()), nb, slices,
+                                         _vp(info.data_ptr()), ctypes.byref(st)), "emul_dgetrf")
+        return (ipiv[:A.m], info, st) if stats else (ipiv[:A.m], info)
+
+    def dgetrs(self, LU, ipiv, B):
+        self._check(self.lib.emul_dgetrs(self.h, LU.m, B.n, _vp(LU.ptr), LU.ld, _vp(ipiv.data_ptr()), _vp(B.ptr),
+                                         B.ld), "emul_dgetrs")
+
+    def dpotrf(self, A, nb=0, slices=7, stats=False):
+        import torch
+        info = torch.zeros(1, dtype=torch.int32, device="cuda")
+        st = Stats()
+        self._check(self.lib.emul_dpotrf(self.h, b"L", A.m, _vp(A.ptr), A.ld, nb, slices, _vp(info.data_ptr()),
+                                         ctypes.byref(st)), "emul_dpotrf")
+        return (info, st) if stats else info
+
+    def dpotrs(self, L, B):
+        self._check(self.lib.emul_dpotrs(self.h, b"L", L.m, B.n, _vp(L.ptr), L.ld, _vp(B.ptr), B.ld),
+                    "emul_dpotrs")
+
+    def backward_error(self, A, x, b):
+        import torch
+        out = torch.zeros(2, dtype=torch.float64, device="cuda")
+        self._check(self.lib.emul_backward_error(self.h, A.m, _vp(A.ptr), A.ld, _vp(x.ptr), _vp(b.ptr),
+                                                 _vp(out.data_ptr())), "emul_backward_error")
+        return out
+
+
+def lib():
+    """A ready handle on torch's current stream (tests use one per session)."""
+    return Emul()
+
+
+def bf16_bits_to_int(t):
+    """BF16 bit patterns (int16 tensor) of small integers -> int64 numpy values."""
+    import torch
+    f = t.view(torch.bfloat16).float().cpu().numpy()
+    return f.astype(np.int64)

@@ -1,0 +1,374 @@
+// C-ABI entry points: handle management, slicing, level sums and the emulated
+// DGEMM (arXiv 2509.23565, Section 2, Eq. 1-4; Section 4, Eq. 7).
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cudaTypedefs.h>
+
+#include "handle.h"
+
+namespace emul {
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+inline long kpad_of(int k) { return (static_cast<long>(k) + 7) / 8 * 8; }
+
+// Sum over the levels L = 2..t-1 of n_L 2^(7(t-1-L)) times 127^2, the worst-case
+// magnitude per unit of k of the Horner state before the last level.
+long double horner_bound_per_k(int s) {
+  const int t = s + 1;
+  long double acc = 0.0L;
+  for (int L = 2; L <= t - 1; ++L) {
+    int nL = 0;
+    for (int p = 1; p <= s; ++p)
+      if (L - p >= 1 && L - p <= s) ++nL;
+    acc = acc * 128.0L + nL;
+  }
+  return acc * 127.0L * 127.0L;
+}
+
+int pairs_at(int s, int L) {
+  int n = 0;
+  for (int p = 1; p <= s; ++p)
+    if (L - p >= 1 && L - p <= s) ++n;
+  return n;
+}
+
+// Build the sweep schedule: levels in ascending order; a level whose pairs fit
+// the exactness budget over the whole K is one job, otherwise it is split into
+// K segments; consecutive single-job levels are paired into one sweep.  In the
+// narrow variant the last level is a separate held sweep.  Returns false if
+// the narrow variant cannot hold the last level in one job.
+bool build_schedule(int s, int nch, bool wide, std::vector<Sweep>& out) {
+  out.clear();
+  const int t = s + 1;
+  auto cmax = [&](int L) {
+    const int n = pairs_at(s, L);
+    int c = kExactBudget / (kBK * n);
+    return c < 1 ? 1 : c;
+  };
+  auto planes = [&](int L) { return L - 1 < s ? L - 1 : s; };
+  int L = 2;
+  while (L <= t) {
+    if (!wide && L == t) {
+      if (nch > cmax(L)) return false;
+      out.push_back(Sweep{0, static_cast<int16_t>(nch), static_cast<int8_t>(L), 0, 1, static_cast<int8_t>(planes(L))});
+      break;
+    }
+    if (nch <= cmax(L)) {
+      const bool next_ok = (L + 1 <= t) && (wide || L + 1 < t) && nch <= cmax(L + 1);
+      if (next_ok) {
+        out.push_back(Sweep{0, static_cast<int16_t>(nch), static_cast<int8_t>(L), static_cast<int8_t>(L + 1), 0,
+                            static_cast<int8_t>(planes(L + 1))});
+        L += 2;
+        continue;
+      }
+      out.push_back(Sweep{0, static_cast<int16_t>(nch), static_cast<int8_t>(L), 0, 0, static_cast<int8_t>(planes(L))});
+      L += 1;
+      continue;
+    }
+    for (int c0 = 0; c0 < nch; c0 += cmax(L)) {
+      const int c1 = c0 + cmax(L) < nch ? c0 + cmax(L) : nch;
+      out.push_back(Sweep{static_cast<int16_t>(c0), static_cast<int16_t>(c1), static_cast<int8_t>(L), 0, 0,
+                          static_cast<int8_t>(planes(L))});
+    }
+    L += 1;
+  }
+  return true;
+}
+
+bool narrow_ok(int s, int k) {
+  if (s > 7) return false;
+  const int nch = (k + kBK - 1) / kBK;
+  std::vector<Sweep> tmp;
+  if (!build_schedule(s, nch, false, tmp)) return false;
+  const long double bound = horner_bound_per_k(s) * static_cast<long double>(nch * kBK);
+  return bound < 9.2e18L;   // below 2^63 with margin
+}
+
+int get_schedule(emul_handle_t h, int s, int nch, bool wide, Sweep** dptr, int* count) {
+  const uint32_t key = (static_cast<uint32_t>(s) << 24) | (static_cast<uint32_t>(wide) << 23) | static_cast<uint32_t>(nch);
+  auto it = h->sched_cache.find(key);
+  if (it != h->sched_cache.end()) {
+    *dptr = it->second.first;
+    *count = it->second.second;
+    return EMUL_OK;
+  }
+  std::vector<Sweep> v;
+  if (!build_schedule(s, nch, wide, v)) return set_error(h, EMUL_INVALID_ARG, "no schedule for this slice count / k");
+  Sweep* d = nullptr;
+  if (cudaMalloc(&d, v.size() * sizeof(Sweep)) != cudaSuccess)
+    return set_error(h, EMUL_NO_WORKSPACE, "schedule allocation failed");
+  if (cudaMemcpy(d, v.data(), v.size() * sizeof(Sweep), cudaMemcpyHostToDevice) != cudaSuccess)
+    return set_error(h, EMUL_CUDA_ERROR, "schedule upload failed");
+  h->sched_cache[key] = {d, static_cast<int>(v.size())};
+  *dptr = d;
+  *count = static_cast<int>(v.size());
+  return EMUL_OK;
+}
+
+int encode_slices_map(emul_handle_t h, CUtensorMap* map, const uint16_t* base, int rows, int k, long kpad, int s,
+                      int box_rows) {
+  auto fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(h->encode_fn);
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(k), static_cast<cuuint64_t>(rows), static_cast<cuuint64_t>(s)};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(kpad) * 2, static_cast<cuuint64_t>(kpad) * 2 * rows};
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(kBK), static_cast<cuuint32_t>(box_rows), 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(h, EMUL_CUDA_ERROR, "cuTensorMapEncodeTiled failed");
+  return EMUL_OK;
+}
+
+__global__ void scale_c_kernel(int m, int n, double alpha, double beta, double* C, long ldc) {
+  const long total = static_cast<long>(m) * n;
+  for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long>(gridDim.x) * blockDim.x) {
+    const int r = static_cast<int>(i % m);
+    const long c = i / m;
+    double* p = C + r + c * ldc;
+    const double ad = __dmul_rn(alpha, 0.0);
+    *p = (beta == 0.0) ? ad : __dadd_rn(ad, __dmul_rn(beta, *p));
+  }
+}
+
+__global__ void zero_levels_kernel(int m, int n, int planes, int32_t* lv, long ldl, long ldp) {
+  const long total = static_cast<long>(m) * n * planes;
+  for (long i = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long>(gridDim.x) * blockDim.x) {
+    const int r = static_cast<int>(i % m);
+    const long rest = i / m;
+    const long c = rest % n;
+    const long p = rest / n;
+    lv[p * ldp + r + c * ldl] = 0;
+  }
+}
+
+}  // namespace
+
+int set_error(emul_handle_t h, int code, const std::string& msg) {
+  if (h) h->last_error = msg;
+  return code;
+}
+
+int check_cuda(emul_handle_t h, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return EMUL_OK;
+  return set_error(h, EMUL_CUDA_ERROR, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int reserve_workspace(emul_handle_t h, size_t bytes) {
+  if (bytes <= h->ws_bytes) return EMUL_OK;
+  if (h->ws) {
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+  }
+  const size_t want = align_up(bytes + bytes / 8);
+  if (cudaMalloc(&h->ws, want) != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(h, EMUL_NO_WORKSPACE, "workspace allocation failed");
+  }
+  h->ws_bytes = want;
+  return EMUL_OK;
+}
+
+size_t gemm_workspace_bytes(int m, int n, int k, int s, bool same_operand) {
+  const size_t kp = static_cast<size_t>(kpad_of(k));
+  size_t b = align_up(static_cast<size_t>(s) * m * kp * 2) + align_up(static_cast<size_t>(m) * 4);
+  if (!same_operand) b += align_up(static_cast<size_t>(s) * n * kp * 2) + align_up(static_cast<size_t>(n) * 4);
+  return b + kAlign;
+}
+
+int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Operand B, double beta, double* C,
+             long ldc, int s, bool lower, int mode, int32_t* levels, long ldl, long ldl_plane, size_t ws_offset) {
+  if (m <= 0 || n <= 0) return EMUL_OK;
+  if (k <= 0) {
+    if (mode == 1) {
+      zero_levels_kernel<<<256, 256, 0, h->stream>>>(m, n, s, levels, ldl, ldl_plane);
+      return check_cuda(h, cudaGetLastError(), "zero levels");
+    }
+    scale_c_kernel<<<1024, 256, 0, h->stream>>>(m, n, alpha, beta, C, ldc);
+    return check_cuda(h, cudaGetLastError(), "scale C");
+  }
+  const bool same = (A.ptr == B.ptr && A.rs == B.rs && A.cs == B.cs && m == n);
+  const size_t need = ws_offset + gemm_workspace_bytes(m, n, k, s, same);
+  int rc = reserve_workspace(h, need);
+  if (rc) return rc;
+  const long kp = kpad_of(k);
+  uint8_t* w = static_cast<uint8_t*>(h->ws) + ws_offset;
+  uint16_t* sa = reinterpret_cast<uint16_t*>(w);
+  w += align_up(static_cast<size_t>(s) * m * kp * 2);
+  int32_t* ea = reinterpret_cast<int32_t*>(w);
+  w += align_up(static_cast<size_t>(m) * 4);
+  uint16_t* sb = sa;
+  int32_t* fb = ea;
+  if (!same) {
+    sb = reinterpret_cast<uint16_t*>(w);
+    w += align_up(static_cast<size_t>(s) * n * kp * 2);
+    fb = reinterpret_cast<int32_t*>(w);
+  }
+  rc = check_cuda(h, launch_split(h->stream, m, k, A.ptr, A.rs, A.cs, s, ea, sa, kp), "split A");
+  if (rc) return rc;
+  if (!same) {
+    rc = check_cuda(h, launch_split(h->stream, n, k, B.ptr, B.rs, B.cs, s, fb, sb, kp), "split B");
+    if (rc) return rc;
+  }
+  if (mode == 1) {
+    zero_levels_kernel<<<256, 256, 0, h->stream>>>(m, n, s, levels, ldl, ldl_plane);
+    rc = check_cuda(h, cudaGetLastError(), "zero levels");
+    if (rc) return rc;
+  }
+  const bool wide = !narrow_ok(s, k);
+  const int nch = (k + kBK - 1) / kBK;
+  Sweep* sched = nullptr;
+  int nsweeps = 0;
+  rc = get_schedule(h, s, nch, wide, &sched, &nsweeps);
+  if (rc) return rc;
+  const int BN = wide ? 64 : 128;
+  CUtensorMap tmA, tmB;
+  rc = encode_slices_map(h, &tmA, sa, m, k, kp, s, 128);
+  if (rc) return rc;
+  rc = encode_slices_map(h, &tmB, sb, n, k, kp, s, BN);
+  if (rc) return rc;
+
+  GemmArgs a{};
+  a.M = m;
+  a.N = n;
+  a.K = k;
+  a.s = s;
+  a.t = s + 1;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.C = C;
+  a.ldc = ldc;
+  a.ea = ea;
+  a.fb = fb;
+  a.sched = sched;
+  a.nsweeps = nsweeps;
+  a.tiles_m = (m + 127) / 128;
+  a.tiles_n = (n + BN - 1) / BN;
+  a.lower = lower ? 1 : 0;
+  a.tri = (lower && !wide && m == n) ? 1 : 0;
+  a.ntiles = a.tri ? a.tiles_m * (a.tiles_m + 1) / 2 : a.tiles_m * a.tiles_n;
+  a.mode = mode;
+  a.levels = levels;
+  a.ldl = ldl;
+  a.ldl_plane = ldl_plane;
+  a.status = h->d_status;
+  a.wait_limit = h->wait_limit;
+
+  const size_t stage = gemm_stage_bytes(wide, s);
+  const size_t budget = 232448 - 1024 - 512;
+  int stages = static_cast<int>(budget / stage);
+  if (stages > 4) stages = 4;
+  if (stages < 2) return set_error(h, EMUL_NOT_SUPPORTED, "slice tiles do not fit in shared memory");
+  const size_t smem = stages * stage + 1024;
+  const int grid = a.ntiles < h->nsm ? a.ntiles : h->nsm;
+  return check_cuda(h, launch_gemm(h->stream, wide, tmA, tmB, a, grid, stages, smem), "gemm kernel");
+}
+
+}  // namespace emul
+
+using emul::Operand;
+
+extern "C" {
+
+int emul_create(emul_handle_t* handle, void* stream) {
+  if (!handle) return EMUL_INVALID_ARG;
+  *handle = nullptr;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return EMUL_CUDA_ERROR;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return EMUL_CUDA_ERROR;
+  if (prop.major != 10 || prop.minor != 3) return EMUL_NOT_SUPPORTED;
+  auto* h = new emul_handle_s();
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->device = dev;
+  h->nsm = prop.multiProcessorCount;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &h->encode_fn, 12000, cudaEnableDefault, &q) !=
+          cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !h->encode_fn) {
+    delete h;
+    return EMUL_CUDA_ERROR;
+  }
+  if (cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess) {
+    delete h;
+    return EMUL_NO_WORKSPACE;
+  }
+  cudaMemset(h->d_status, 0, sizeof(int));
+  *handle = h;
+  return EMUL_OK;
+}
+
+int emul_destroy(emul_handle_t h) {
+  if (!h) return EMUL_INVALID_ARG;
+  cudaStreamSynchronize(h->stream);
+  for (auto& kv : h->sched_cache) cudaFree(kv.second.first);
+  if (h->ws) cudaFree(h->ws);
+  if (h->d_status) cudaFree(h->d_status);
+  delete h;
+  return EMUL_OK;
+}
+
+int emul_set_stream(emul_handle_t h, void* stream) {
+  if (!h) return EMUL_INVALID_ARG;
+  h->stream = static_cast<cudaStream_t>(stream);
+  return EMUL_OK;
+}
+
+const char* emul_last_error(emul_handle_t h) { return h ? h->last_error.c_str() : "null handle"; }
+
+int emul_sync_status(emul_handle_t h) {
+  if (!h) return EMUL_INVALID_ARG;
+  int rc = emul::check_cuda(h, cudaStreamSynchronize(h->stream), "stream synchronize");
+  if (rc) return rc;
+  int st = 0;
+  rc = emul::check_cuda(h, cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost), "status read");
+  if (rc) return rc;
+  cudaMemset(h->d_status, 0, sizeof(int));
+  if (st != 0) return emul::set_error(h, st, "a device-side wait gave up");
+  return EMUL_OK;
+}
+
+size_t emul_workspace_bytes(emul_handle_t h) { return h ? h->ws_bytes : 0; }
+
+int emul_split(emul_handle_t h, int rows, int k, const double* X, long rs, long cs, int slices, int32_t* exps,
+               uint16_t* slice_out, long ldk) {
+  if (!h) return EMUL_INVALID_ARG;
+  if (rows < 0 || k < 0 || slices < 1 || slices > emul::kMaxSlices || ldk < k || ldk % 8 != 0 ||
+      (rs != 1 && cs != 1) || (rows > 0 && (!X || !exps || !slice_out)))
+    return emul::set_error(h, EMUL_INVALID_ARG, "emul_split: invalid argument");
+  return emul::check_cuda(h, emul::launch_split(h->stream, rows, k, X, rs, cs, slices, exps, slice_out, ldk),
+                          "split");
+}
+
+int emul_level_sums(emul_handle_t h, int m, int n, int k, const double* A, int lda, const double* B, int ldb,
+                    int slices, int32_t* levels, int ldl, long ldl_plane) {
+  if (!h) return EMUL_INVALID_ARG;
+  if (m < 0 || n < 0 || k < 0 || slices < 1 || slices > emul::kMaxSlices || lda < (m > 1 ? m : 1) ||
+      ldb < (k > 1 ? k : 1) || ldl < (m > 1 ? m : 1) || ldl_plane < static_cast<long>(ldl) * n || !levels ||
+      k > 16384 * 4)
+    return emul::set_error(h, EMUL_INVALID_ARG, "emul_level_sums: invalid argument");
+  return emul::gemm_run(h, m, n, k, 1.0, Operand{A, 1, lda}, Operand{B, ldb, 1}, 0.0, nullptr, 0, slices, false, 1,
+                        levels, ldl, ldl_plane);
+}
+
+int emul_dgemm(emul_handle_t h, int m, int n, int k, double alpha, const double* A, int lda, const double* B,
+               int ldb, double beta, double* C, int ldc, int slices) {
+  if (!h) return EMUL_INVALID_ARG;
+  if (m < 0 || n < 0 || k < 0 || slices < 1 || slices > emul::kMaxSlices || lda < (m > 1 ? m : 1) ||
+      ldb < (k > 1 ? k : 1) || ldc < (m > 1 ? m : 1) || (m > 0 && n > 0 && !C) ||
+      (m > 0 && n > 0 && k > 0 && (!A || !B)) || k > 16384 * 4)
+    return emul::set_error(h, EMUL_INVALID_ARG, "emul_dgemm: invalid argument");
+  return emul::gemm_run(h, m, n, k, alpha, Operand{A, 1, lda}, Operand{B, ldb, 1}, beta, C, ldc, slices, false, 0,
+                        nullptr, 0, 0);
+}
+
+}  // extern "C"

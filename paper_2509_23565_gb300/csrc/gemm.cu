@@ -1,0 +1,410 @@
+// Slice-pair products on tcgen05 tensor cores with the fused exact
+// recombination and C update (arXiv 2509.23565, Section 2, Eq. 2 with the
+// truncation threshold t; Section 4, Eq. 7 when alpha = -1, beta = 1).
+//
+// For an output tile (128 rows x BN columns) the level sums
+//   I_L = sum_{p+q=L} SA_p SB_q^T,  L = 2..t,
+// are accumulated in TMEM as FP32.  The slices are integers |S| <= 127 held as
+// BF16, so every product and every partial sum is an integer; an accumulator
+// never receives more than 1040 * 127^2 < 2^24 in magnitude (the schedule
+// splits K where needed), so the FP32 sums are exact.  The epilogue converts
+// each drained level exactly to an integer and folds it into a Horner state
+// R = R * 2^7 + I_L (int64, or 128-bit for the wide variant); the final value
+// T = sum_L I_L 2^(7(t-L)) is rounded once to FP64 in integer arithmetic,
+//   D = RN(T * 2^(e_i + f_j - 7t)),
+// and C = RN(RN(alpha D) + RN(beta C)) is written straight back.
+//
+// Warp roles (384 threads): warp 0 issues TMA loads of the slice tiles of each
+// K chunk into a ring of shared-memory stages; warp 1 owns TMEM (4 accumulator
+// slots) and issues the MMAs; warps 4-11 drain the slots and write C.  The
+// first warpgroup gives registers to the two epilogue warpgroups (setmaxnreg).  Sweeps
+// of one or two levels share the staged tiles of a chunk; two slots are filled
+// while the other two are drained.  All waits are bounded.
+#include <cstdint>
+#include <type_traits>
+
+#include "emul_internal.h"
+#include "ptx.cuh"
+
+namespace emul {
+
+namespace {
+
+constexpr int kThreads = 384;          // 3 warpgroups: producer/MMA, 2 x epilogue
+constexpr int kLaunchRegs = 168;        // 384 x 168 = 64512 registers at launch
+constexpr int kLowRegs = 40;            // producer warpgroup after setmaxnreg.dec
+constexpr int kHighRegs = 232;          // epilogue warpgroups: 128*40 + 256*232 = 64512
+constexpr int kSlots = 4;
+constexpr int kEpiWarps = 8;
+constexpr int kMaxStages = 4;
+constexpr int kStatusTimeout = -4;
+
+template <bool WIDE>
+struct Cfg {
+  static constexpr int BM = 128;
+  static constexpr int BN = WIDE ? 64 : 128;
+  static constexpr int CPT = BN / 2;                  // columns per epilogue thread
+  static constexpr uint32_t A_TILE = BM * kBK * 2;    // bytes
+  static constexpr uint32_t B_TILE = BN * kBK * 2;
+  static constexpr uint32_t TMEM_COLS = kSlots * BN;
+  using State = typename std::conditional<WIDE, __int128, long long>::type;
+};
+
+// Correctly rounded double of T * 2^sh (round to nearest even), computed with
+// integer operations on the IEEE-754 fields (overflow gives +-inf, results
+// below the normal range are rounded as subnormals).
+__device__ __forceinline__ double rn_scaled(__int128 T, int sh) {
+  if (T == 0) return 0.0;
+  const bool neg = T < 0;
+  const unsigned __int128 mag = neg ? (unsigned __int128)(-(T + 1)) + 1u : (unsigned __int128)T;
+  const uint64_t hi = (uint64_t)(mag >> 64), lo = (uint64_t)mag;
+  const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+  const int E = msb + sh;
+  const uint64_t sign = neg ? 0x8000000000000000ull : 0ull;
+  if (E > 1023) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
+  const int keep = (E >= -1022) ? msb - 52 : -1074 - sh;   // bit of mag kept as the last mantissa bit
+  uint64_t q;
+  if (keep <= 0) {
+    q = (uint64_t)(mag << (-keep));
+  } else {
+    if (keep > msb + 1) return __longlong_as_double((long long)sign);   // below half the smallest subnormal
+    q = (uint64_t)(mag >> keep);
+    const unsigned __int128 rem = mag - ((unsigned __int128)q << keep);
+    const unsigned __int128 half = (unsigned __int128)1 << (keep - 1);
+    if (rem > half || (rem == half && (q & 1ull))) q += 1;
+  }
+  const uint64_t bits = (E >= -1022) ? ((uint64_t)(E + 1022) << 52) + q : q;
+  return __longlong_as_double((long long)(sign | bits));
+}
+
+__device__ __forceinline__ int f2i(uint32_t r) { return __float2int_rn(__uint_as_float(r)); }
+
+// D = RN(T * 2^(e + f - 7t)) (NaN for a non-finite scale), then
+// out = RN(RN(alpha D) + RN(beta C)); alpha = +-1 and beta in {0, 1} skip the
+// exact multiplications.
+__device__ __forceinline__ double finish(const GemmArgs& a, __int128 T, int e_row, int col, int alpha_mode,
+                                         int beta_mode, double c_old) {
+  const int f = a.fb[col];
+  double D;
+  if (e_row == kNonFinite || f == kNonFinite)
+    D = __longlong_as_double(0x7FF8000000000000ll);
+  else
+    D = rn_scaled(T, e_row + f - 7 * a.t);
+  const double ad = alpha_mode == 1 ? D : (alpha_mode == -1 ? -D : __dmul_rn(a.alpha, D));
+  if (beta_mode == 0) return ad;
+  return __dadd_rn(ad, beta_mode == 1 ? c_old : __dmul_rn(a.beta, c_old));
+}
+
+__device__ __forceinline__ void tile_coords(const GemmArgs& a, int tile, int& tm, int& tn) {
+  if (a.tri) {
+    // lower-triangular enumeration of square tiles: tile = tm(tm+1)/2 + tn, tn <= tm
+    int r = (int)((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
+    while ((long)r * (r + 1) / 2 > tile) --r;
+    while ((long)(r + 1) * (r + 2) / 2 <= tile) ++r;
+    tm = r;
+    tn = tile - r * (r + 1) / 2;
+  } else {
+    tm = tile % a.tiles_m;
+    tn = tile / a.tiles_m;
+  }
+}
+
+__device__ __forceinline__ bool aborted(volatile int* flag) { return *flag != 0; }
+
+__device__ __forceinline__ void raise_timeout(const GemmArgs& a, volatile int* flag) {
+  atomicExch(a.status, kStatusTimeout);
+  *flag = 1;
+}
+
+}  // namespace
+
+template <bool WIDE>
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs a,
+                int stages) {
+  using Cf = Cfg<WIDE>;
+  using State = typename Cf::State;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t stage_full[kMaxStages], stage_empty[kMaxStages];
+  __shared__ __align__(8) uint64_t slot_full[kSlots], slot_empty[kSlots], mma_done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = a.s;
+  const uint32_t stage_bytes = (uint32_t)s * (Cf::A_TILE + Cf::B_TILE);
+  volatile int* abortp = &abort_flag;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < stages; ++i) {
+      mbar_init(&stage_full[i], 1);
+      mbar_init(&stage_empty[i], 1);
+    }
+    for (int i = 0; i < kSlots; ++i) {
+      mbar_init(&slot_full[i], 1);
+      mbar_init(&slot_empty[i], kEpiWarps);
+    }
+    mbar_init(&mma_done, 1);
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) tmem_alloc(&tmem_base, Cf::TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  if (warp < 4) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kLowRegs));
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      prefetch_tmap(&tmA);
+      prefetch_tmap(&tmB);
+      long it = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+        int tm, tn;
+        tile_coords(a, tile, tm, tn);
+        const int m0 = tm * Cf::BM, n0 = tn * Cf::BN;
+        for (int sw = 0; sw < a.nsweeps && ok; ++sw) {
+          const Sweep S = a.sched[sw];
+          for (int kc = S.k0c; kc < S.k1c; ++kc, ++it) {
+            const int st = (int)(it % stages);
+            const uint32_t par = (uint32_t)((it / stages) & 1) ^ 1u;
+            if (aborted(abortp) || !mbar_wait(&stage_empty[st], par, a.wait_limit)) {
+              if (!aborted(abortp)) raise_timeout(a, abortp);
+              ok = false;
+              break;
+            }
+            uint8_t* base = smem + (size_t)st * stage_bytes;
+            mbar_arrive_expect_tx(&stage_full[st], (uint32_t)S.nplanes * (Cf::A_TILE + Cf::B_TILE));
+            for (int p = 0; p < S.nplanes; ++p) {
+              tma_load_3d(base + p * Cf::A_TILE, &tmA, &stage_full[st], kc * kBK, m0, p);
+              tma_load_3d(base + s * Cf::A_TILE + p * Cf::B_TILE, &tmB, &stage_full[st], kc * kBK, n0, p);
+            }
+          }
+        }
+      }
+      if (!ok) {
+        // wait (bounded) for the copies still in flight before the block exits
+        for (long j = (it - stages > 0 ? it - stages : 0); j < it; ++j)
+          mbar_wait(&stage_full[j % stages], (uint32_t)((j / stages) & 1), a.wait_limit / 8);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16_f32(128, Cf::BN);
+      long it = 0, jc = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+        for (int sw = 0; sw < a.nsweeps && ok; ++sw) {
+          const Sweep S = a.sched[sw];
+          const int nj = S.L1 ? 2 : 1;
+          const int lev[2] = {S.L0, S.L1};
+          uint32_t dcol[2];
+          for (int j = 0; j < nj; ++j) {
+            const long u = jc + j;
+            const int slot = (int)(u % kSlots);
+            dcol[j] = tmem + (uint32_t)(slot * Cf::BN);
+            if (aborted(abortp) || !mbar_wait(&slot_empty[slot], (uint32_t)((u / kSlots) & 1) ^ 1u, a.wait_limit)) {
+              if (!aborted(abortp)) raise_timeout(a, abortp);
+              ok = false;
+              break;
+            }
+          }
+          if (!ok) break;
+          tc_fence_after();
+          for (int kc = S.k0c; kc < S.k1c; ++kc, ++it) {
+            const int st = (int)(it % stages);
+            if (aborted(abortp) || !mbar_wait(&stage_full[st], (uint32_t)((it / stages) & 1), a.wait_limit)) {
+              if (!aborted(abortp)) raise_timeout(a, abortp);
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t base = smem_u32(smem + (size_t)st * stage_bytes);
+            for (int j = 0; j < nj; ++j) {
+              const int L = lev[j];
+              const int pb = L - s > 1 ? L - s : 1;
+              const int pe = L - 1 < s ? L - 1 : s;
+              for (int p = pb; p <= pe; ++p) {
+                const int q = L - p;
+                const uint32_t aa = base + (uint32_t)(p - 1) * Cf::A_TILE;
+                const uint32_t ba = base + (uint32_t)s * Cf::A_TILE + (uint32_t)(q - 1) * Cf::B_TILE;
+#pragma unroll
+                for (int kk = 0; kk < kBK / 16; ++kk) {
+                  const uint32_t acc = (kc != S.k0c || p != pb || kk != 0) ? 1u : 0u;
+                  mma_bf16(dcol[j], umma_desc(aa + kk * 32, 64, 4), umma_desc(ba + kk * 32, 64, 4), idesc, acc);
+                }
+              }
+            }
+            mma_commit(&stage_empty[st]);
+          }
+          if (!ok) break;
+          for (int j = 0; j < nj; ++j) mma_commit(&slot_full[(jc + j) % kSlots]);
+          jc += nj;
+        }
+      }
+      // every MMA issued by this thread must be complete before TMEM is released
+      mma_commit(&mma_done);
+      mbar_wait(&mma_done, 0, a.wait_limit);
+    }
+  }
+  } else {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kHighRegs));
+    // ------------------------------------------------------------ epilogue
+    const int ew = warp - 4;
+    const int quarter = warp & 3;
+    const int half = ew >> 2;
+    const int row_t = quarter * 32 + lane;
+    const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+    constexpr int CPT = Cf::CPT;
+    const int alpha_mode = (a.alpha == 1.0) ? 1 : (a.alpha == -1.0 ? -1 : 0);
+    const int beta_mode = (a.beta == 0.0) ? 0 : (a.beta == 1.0 ? 1 : 2);
+    State R[CPT];
+    long jc = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+      int tm, tn;
+      tile_coords(a, tile, tm, tn);
+      const int row = tm * Cf::BM + row_t;
+      const int col0 = tn * Cf::BN + half * CPT;
+      const int e_row = row < a.M ? a.ea[row] : 0;
+#pragma unroll
+      for (int c = 0; c < CPT; ++c) R[c] = 0;
+      int prevL = -1;
+      bool held_final = false;
+      for (int sw = 0; sw < a.nsweeps && ok; ++sw) {
+        const Sweep S = a.sched[sw];
+        const int nj = S.L1 ? 2 : 1;
+        for (int j = 0; j < nj; ++j) {
+          const int L = j ? S.L1 : S.L0;
+          const int slot = (int)(jc % kSlots);
+          if (aborted(abortp) || !mbar_wait(&slot_full[slot], (uint32_t)((jc / kSlots) & 1), a.wait_limit)) {
+            if (!aborted(abortp)) raise_timeout(a, abortp);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t taddr = tmem + lane_addr + (uint32_t)(slot * Cf::BN + half * CPT);
+          if (a.mode == 1) {
+            // level sums out (exact int32), added so that K segments accumulate
+#pragma unroll
+            for (int c16 = 0; c16 < CPT / 16; ++c16) {
+              uint32_t r[16];
+              tmem_ld16(taddr + c16 * 16, r);
+              tmem_ld_wait();
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj) {
+                const int col = col0 + c16 * 16 + jj;
+                if (row < a.M && col < a.N) {
+                  int32_t* lp = a.levels + (long)(L - 2) * a.ldl_plane + row + (long)col * a.ldl;
+                  *lp += f2i(r[jj]);
+                }
+              }
+            }
+          } else if (S.last) {
+            // final step: T = R * 2^7 + I_t, rounded once, C updated in place
+            held_final = true;
+#pragma unroll
+            for (int c8 = 0; c8 < CPT / 8; ++c8) {
+              uint32_t r[8];
+              tmem_ld8(taddr + c8 * 8, r);
+              double cv[8];
+              const bool rowok = row < a.M;
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj) {
+                const int col = col0 + c8 * 8 + jj;
+                cv[jj] = (beta_mode != 0 && rowok && col < a.N) ? a.C[row + (long)col * a.ldc] : 0.0;
+              }
+              tmem_ld_wait();
+#pragma unroll
+              for (int jj = 0; jj < 8; ++jj) {
+                const int c = c8 * 8 + jj;
+                const int col = col0 + c;
+                if (!rowok || col >= a.N || (a.lower && row < col)) continue;
+                const __int128 T = (__int128)R[c] * 128 + (__int128)f2i(r[jj]);
+                a.C[row + (long)col * a.ldc] =
+                    finish(a, T, e_row, col, alpha_mode, beta_mode, cv[jj]);
+              }
+            }
+          } else {
+            if (L != prevL) {
+#pragma unroll
+              for (int c = 0; c < CPT; ++c) R[c] = R[c] * (State)128;
+              prevL = L;
+            }
+#pragma unroll
+            for (int c16 = 0; c16 < CPT / 16; ++c16) {
+              uint32_t r[16];
+              tmem_ld16(taddr + c16 * 16, r);
+              tmem_ld_wait();
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj) R[c16 * 16 + jj] += (State)f2i(r[jj]);
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&slot_empty[slot]);
+          ++jc;
+        }
+      }
+      if (ok && a.mode == 0 && !held_final) {
+        // every level was folded into R (wide variant): T = R
+#pragma unroll
+        for (int c8 = 0; c8 < CPT / 8; ++c8) {
+          double cv[8];
+          const bool rowok = row < a.M;
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const int col = col0 + c8 * 8 + jj;
+            cv[jj] = (beta_mode != 0 && rowok && col < a.N) ? a.C[row + (long)col * a.ldc] : 0.0;
+          }
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const int c = c8 * 8 + jj;
+            const int col = col0 + c;
+            if (!rowok || col >= a.N || (a.lower && row < col)) continue;
+            a.C[row + (long)col * a.ldc] = finish(a, (__int128)R[c], e_row, col, alpha_mode, beta_mode, cv[jj]);
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, Cf::TMEM_COLS);
+  }
+}
+
+size_t gemm_stage_bytes(bool wide, int s) {
+  return wide ? (size_t)s * (Cfg<true>::A_TILE + Cfg<true>::B_TILE)
+              : (size_t)s * (Cfg<false>::A_TILE + Cfg<false>::B_TILE);
+}
+
+cudaError_t launch_gemm(cudaStream_t st, bool wide, const CUtensorMap& tmA, const CUtensorMap& tmB,
+                        const GemmArgs& args, int grid, int stages, size_t smem_bytes) {
+  // The register hand-over between warpgroups is only valid if the block was
+  // launched with exactly kLaunchRegs registers per thread.
+  cudaFuncAttributes fa;
+  cudaError_t ea = cudaFuncGetAttributes(&fa, wide ? (const void*)gemm_kernel<true> : (const void*)gemm_kernel<false>);
+  if (ea != cudaSuccess) return ea;
+  if (fa.numRegs != kLaunchRegs) return cudaErrorInvalidConfiguration;
+  if (wide) {
+    cudaError_t e = cudaFuncSetAttribute(gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    gemm_kernel<true><<<grid, kThreads, smem_bytes, st>>>(tmA, tmB, args, stages);
+  } else {
+    cudaError_t e = cudaFuncSetAttribute(gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    if (e != cudaSuccess) return e;
+    gemm_kernel<false><<<grid, kThreads, smem_bytes, st>>>(tmA, tmB, args, stages);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace emul

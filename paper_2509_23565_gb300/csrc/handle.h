@@ -1,0 +1,51 @@
+// Handle state and the internal product driver shared by the C-ABI sources.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "../../include/emul.h"
+#include "emul_internal.h"
+
+struct emul_handle_s {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int nsm = 0;
+  int* d_status = nullptr;          // device status word written by kernels
+  void* ws = nullptr;               // workspace (device)
+  size_t ws_bytes = 0;
+  std::map<uint32_t, std::pair<emul::Sweep*, int>> sched_cache;   // (s, chunks, wide) -> device schedule
+  std::string last_error;
+  void* encode_fn = nullptr;        // cuTensorMapEncodeTiled
+  long long wait_limit = 2000000000LL;
+};
+
+namespace emul {
+
+// A GEMM operand viewed as `rows` x `k`: element (r, c) at ptr[r*rs + c*cs].
+struct Operand {
+  const double* ptr;
+  long rs, cs;
+};
+
+int set_error(emul_handle_t h, int code, const std::string& msg);
+int check_cuda(emul_handle_t h, cudaError_t e, const char* what);
+
+// Grow the workspace to at least `bytes` (synchronises the device when it grows).
+int reserve_workspace(emul_handle_t h, size_t bytes);
+// Workspace bytes a product of this shape needs (slices, scales).
+size_t gemm_workspace_bytes(int m, int n, int k, int s, bool same_operand);
+
+// C <- beta*C + alpha*(A B^T-view) with the emulated product.  A: m x k operand,
+// B: n x k operand (row j of the operand is column j of the mathematical B).
+// `ws_offset` places the slices inside the workspace (callers running several
+// products back to back on one stream may share offset 0).
+int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Operand B, double beta, double* C,
+             long ldc, int s, bool lower, int mode, int32_t* levels, long ldl, long ldl_plane, size_t ws_offset = 0);
+
+}  // namespace emul
