@@ -139,6 +139,24 @@ int emul_dpotrs(emul_handle_t h, char uplo, int n, int nrhs, const double* L, in
 int emul_backward_error(emul_handle_t h, int n, const double* A, int lda, const double* x, const double* b,
                         double* out);
 
+/* ------------------------------------------------------------ profiling --
+ * Counters of the work this handle enqueued, for benchmarks (no paper
+ * counterpart).  While enabled, every launch of the slice-pair product kernel
+ * is bracketed by CUDA events on the handle's stream.
+ */
+typedef struct emul_profile {
+  long long kernel_launches;    /* kernels launched by this handle since the last read */
+  long long product_launches;   /* launches of the slice-pair product kernel */
+  double product_ms;            /* their summed device time (CUDA events) */
+  double product_tensor_flops;  /* sum of 2 m n k P (P = s(s+1)/2 slice-pair products) */
+  double product_bytes;         /* algorithmic bytes: C read + write (8 B each) and the slices read */
+} emul_profile;
+
+/* Enable (1) or disable (0) event timing of the product kernel. */
+int emul_profile_enable(emul_handle_t h, int enable);
+/* Synchronise the handle's stream, return the counters and reset them. */
+int emul_profile_read(emul_handle_t h, emul_profile* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -39,6 +39,8 @@ SIGNATURES = {
     "emul_dpotrf": (_c_int, [_vp, _c_char, _c_int, _vp, _c_int, _c_int, _c_int, _vp, _vp]),
     "emul_dpotrs": (_c_int, [_vp, _c_char, _c_int, _c_int, _vp, _c_int, _vp, _c_int]),
     "emul_backward_error": (_c_int, [_vp, _c_int, _vp, _c_int, _vp, _vp, _vp]),
+    "emul_profile_enable": (_c_int, [_vp, _c_int]),
+    "emul_profile_read": (_c_int, [_vp, _vp]),
 }
 
 _LIB = None
@@ -51,6 +53,12 @@ class EmulError(RuntimeError):
 class Stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("slices_min", ctypes.c_int), ("slices_max", ctypes.c_int),
                 ("checks_failed", ctypes.c_int), ("seconds", ctypes.c_double)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_longlong), ("product_launches", ctypes.c_longlong),
+                ("product_ms", ctypes.c_double), ("product_tensor_flops", ctypes.c_double),
+                ("product_bytes", ctypes.c_double)]
 
 
 def load():
@@ -132,6 +140,14 @@ class Emul:
 
     def sync_status(self):
         self._check(self.lib.emul_sync_status(self.h), "emul_sync_status")
+
+    def profile_enable(self, on=True):
+        self._check(self.lib.emul_profile_enable(self.h, 1 if on else 0), "emul_profile_enable")
+
+    def profile_read(self):
+        p = Profile()
+        self._check(self.lib.emul_profile_read(self.h, ctypes.byref(p)), "emul_profile_read")
+        return {k: getattr(p, k) for k, _ in Profile._fields_}
 
     def workspace_bytes(self):
         return int(self.lib.emul_workspace_bytes(self.h))

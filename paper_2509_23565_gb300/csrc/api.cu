@@ -81,13 +81,15 @@ bool build_schedule(int s, int nch, bool wide, std::vector<Sweep>& out) {
   return true;
 }
 
+// The narrow variant keeps the Horner state in int64 and rounds T = R 2^7 + I
+// with a 64-bit magnitude: it needs |R| < 2^57 and the last level in one job.
 bool narrow_ok(int s, int k) {
   if (s > 7) return false;
   const int nch = (k + kBK - 1) / kBK;
   std::vector<Sweep> tmp;
   if (!build_schedule(s, nch, false, tmp)) return false;
   const long double bound = horner_bound_per_k(s) * static_cast<long double>(nch * kBK);
-  return bound < 9.2e18L;   // below 2^63 with margin
+  return bound < 1.44e17L;   // 2^57
 }
 
 int get_schedule(emul_handle_t h, int s, int nch, bool wide, Sweep** dptr, int* count) {
@@ -191,9 +193,11 @@ int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Oper
   if (k <= 0) {
     if (mode == 1) {
       zero_levels_kernel<<<256, 256, 0, h->stream>>>(m, n, s, levels, ldl, ldl_plane);
+      h->launches++;
       return check_cuda(h, cudaGetLastError(), "zero levels");
     }
     scale_c_kernel<<<1024, 256, 0, h->stream>>>(m, n, alpha, beta, C, ldc);
+    h->launches++;
     return check_cuda(h, cudaGetLastError(), "scale C");
   }
   const bool same = (A.ptr == B.ptr && A.rs == B.rs && A.cs == B.cs && m == n);
@@ -215,11 +219,14 @@ int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Oper
   }
   rc = check_cuda(h, launch_split(h->stream, m, k, A.ptr, A.rs, A.cs, s, ea, sa, kp), "split A");
   if (rc) return rc;
+  h->launches++;
   if (!same) {
     rc = check_cuda(h, launch_split(h->stream, n, k, B.ptr, B.rs, B.cs, s, fb, sb, kp), "split B");
     if (rc) return rc;
+    h->launches++;
   }
   if (mode == 1) {
+    h->launches++;
     zero_levels_kernel<<<256, 256, 0, h->stream>>>(m, n, s, levels, ldl, ldl_plane);
     rc = check_cuda(h, cudaGetLastError(), "zero levels");
     if (rc) return rc;
@@ -270,7 +277,31 @@ int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Oper
   if (stages < 2) return set_error(h, EMUL_NOT_SUPPORTED, "slice tiles do not fit in shared memory");
   const size_t smem = stages * stage + 1024;
   const int grid = a.ntiles < h->nsm ? a.ntiles : h->nsm;
-  return check_cuda(h, launch_gemm(h->stream, wide, tmA, tmB, a, grid, stages, smem), "gemm kernel");
+  emul_handle_s::ProfRec rec{};
+  if (h->prof) {
+    for (int i = 0; i < 2; ++i) {
+      cudaEvent_t ev;
+      if (!h->event_pool.empty()) {
+        ev = h->event_pool.back();
+        h->event_pool.pop_back();
+      } else if (cudaEventCreate(&ev) != cudaSuccess) {
+        return set_error(h, EMUL_CUDA_ERROR, "event creation failed");
+      }
+      (i == 0 ? rec.e0 : rec.e1) = ev;
+    }
+    const double P = static_cast<double>(s) * (s + 1) / 2.0;
+    const double cells = lower ? 0.5 * m * (double)n : static_cast<double>(m) * n;
+    rec.flops = 2.0 * cells * k * P;
+    rec.bytes = cells * (beta != 0.0 ? 16.0 : 8.0) + static_cast<double>(s) * 2.0 * k * (m + (same ? 0 : n));
+    cudaEventRecord(rec.e0, h->stream);
+  }
+  rc = check_cuda(h, launch_gemm(h->stream, wide, tmA, tmB, a, grid, stages, smem), "gemm kernel");
+  h->launches++;
+  if (h->prof) {
+    cudaEventRecord(rec.e1, h->stream);
+    h->recs.push_back(rec);
+  }
+  return rc;
 }
 
 }  // namespace emul
@@ -311,6 +342,11 @@ int emul_destroy(emul_handle_t h) {
   if (!h) return EMUL_INVALID_ARG;
   cudaStreamSynchronize(h->stream);
   for (auto& kv : h->sched_cache) cudaFree(kv.second.first);
+  for (auto& r : h->recs) {
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+  }
+  for (auto ev : h->event_pool) cudaEventDestroy(ev);
   if (h->ws) cudaFree(h->ws);
   if (h->d_status) cudaFree(h->d_status);
   delete h;
@@ -339,12 +375,41 @@ int emul_sync_status(emul_handle_t h) {
 
 size_t emul_workspace_bytes(emul_handle_t h) { return h ? h->ws_bytes : 0; }
 
+int emul_profile_enable(emul_handle_t h, int enable) {
+  if (!h) return EMUL_INVALID_ARG;
+  h->prof = enable != 0;
+  return EMUL_OK;
+}
+
+int emul_profile_read(emul_handle_t h, emul_profile* out) {
+  if (!h || !out) return EMUL_INVALID_ARG;
+  int rc = emul::check_cuda(h, cudaStreamSynchronize(h->stream), "stream synchronize");
+  if (rc) return rc;
+  emul_profile p{};
+  p.kernel_launches = h->launches;
+  for (auto& r : h->recs) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.e0, r.e1);
+    p.product_launches++;
+    p.product_ms += ms;
+    p.product_tensor_flops += r.flops;
+    p.product_bytes += r.bytes;
+    h->event_pool.push_back(r.e0);
+    h->event_pool.push_back(r.e1);
+  }
+  h->recs.clear();
+  h->launches = 0;
+  *out = p;
+  return EMUL_OK;
+}
+
 int emul_split(emul_handle_t h, int rows, int k, const double* X, long rs, long cs, int slices, int32_t* exps,
                uint16_t* slice_out, long ldk) {
   if (!h) return EMUL_INVALID_ARG;
   if (rows < 0 || k < 0 || slices < 1 || slices > emul::kMaxSlices || ldk < k || ldk % 8 != 0 ||
       (rs != 1 && cs != 1) || (rows > 0 && (!X || !exps || !slice_out)))
     return emul::set_error(h, EMUL_INVALID_ARG, "emul_split: invalid argument");
+  h->launches++;
   return emul::check_cuda(h, emul::launch_split(h->stream, rows, k, X, rs, cs, slices, exps, slice_out, ldk),
                           "split");
 }

@@ -77,22 +77,54 @@ __device__ __forceinline__ double rn_scaled(__int128 T, int sh) {
   return __longlong_as_double((long long)(sign | bits));
 }
 
+// Fast path of rn_scaled for T = R * 2^7 + I with |R| < 2^57 and |I| < 2^24
+// (the narrow variant), where |T| < 2^64 fits an unsigned 64-bit magnitude.
+// Results outside the normal exponent range take the generic path.
+__device__ __forceinline__ double rn_scaled_r7(long long R, int I, int sh) {
+  const bool rneg = R < 0;
+  const unsigned long long aR = rneg ? 0ull - (unsigned long long)R : (unsigned long long)R;
+  const long long Is = rneg ? -(long long)I : (long long)I;
+  unsigned long long u = (aR << 7) + (unsigned long long)Is;
+  bool neg = rneg;
+  if (aR < (1ull << 17) && (long long)u < 0) {   // small R: the sum may change sign
+    u = 0ull - u;
+    neg = !neg;
+  }
+  if (u == 0ull) return 0.0;
+  const int lz = __clzll((long long)u);
+  const int E = 63 - lz + sh;
+  if (E < -1022 || E > 1023) return rn_scaled((__int128)R * 128 + (__int128)I, sh);
+  const unsigned long long nrm = u << lz;                     // leading one at bit 63
+  const unsigned long long rb = nrm & 0x7FFull;               // bits below the 53-bit mantissa
+  const unsigned long long q = (nrm >> 11) + ((rb + 0x3FFull + ((nrm >> 11) & 1ull)) >> 11);
+  const unsigned long long bits = ((unsigned long long)(E + 1022) << 52) + q;
+  return __longlong_as_double((long long)(bits | (neg ? 0x8000000000000000ull : 0ull)));
+}
+
 __device__ __forceinline__ int f2i(uint32_t r) { return __float2int_rn(__uint_as_float(r)); }
+
+__device__ __forceinline__ double neg_d(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 
 // D = RN(T * 2^(e + f - 7t)) (NaN for a non-finite scale), then
 // out = RN(RN(alpha D) + RN(beta C)); alpha = +-1 and beta in {0, 1} skip the
 // exact multiplications.
-__device__ __forceinline__ double finish(const GemmArgs& a, __int128 T, int e_row, int col, int alpha_mode,
-                                         int beta_mode, double c_old) {
-  const int f = a.fb[col];
-  double D;
-  if (e_row == kNonFinite || f == kNonFinite)
-    D = __longlong_as_double(0x7FF8000000000000ll);
-  else
-    D = rn_scaled(T, e_row + f - 7 * a.t);
-  const double ad = alpha_mode == 1 ? D : (alpha_mode == -1 ? -D : __dmul_rn(a.alpha, D));
-  if (beta_mode == 0) return ad;
-  return __dadd_rn(ad, beta_mode == 1 ? c_old : __dmul_rn(a.beta, c_old));
+// Update modes of C: kSub: C - D (alpha = -1, beta = 1); kSet: D (alpha = 1,
+// beta = 0); kGeneral: RN(RN(alpha D) + RN(beta C)) (beta = 0: RN(alpha D)).
+enum UpdMode { kGeneral = 0, kSub = 1, kSet = 2 };
+
+template <int UPD>
+__device__ __forceinline__ double apply_update(const GemmArgs& a, double D, double c_old) {
+  if (UPD == kSub) return __dadd_rn(c_old, neg_d(D));
+  if (UPD == kSet) return D;
+  const double ad = __dmul_rn(a.alpha, D);
+  if (a.beta == 0.0) return ad;
+  return __dadd_rn(ad, __dmul_rn(a.beta, c_old));
 }
 
 __device__ __forceinline__ void tile_coords(const GemmArgs& a, int tile, int& tm, int& tn) {
@@ -118,7 +150,7 @@ __device__ __forceinline__ void raise_timeout(const GemmArgs& a, volatile int* f
 
 }  // namespace
 
-template <bool WIDE>
+template <bool WIDE, int UPD>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs a,
                 int stages) {
@@ -262,8 +294,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int row_t = quarter * 32 + lane;
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
     constexpr int CPT = Cf::CPT;
-    const int alpha_mode = (a.alpha == 1.0) ? 1 : (a.alpha == -1.0 ? -1 : 0);
-    const int beta_mode = (a.beta == 0.0) ? 0 : (a.beta == 1.0 ? 1 : 2);
+    const bool needs_c = (UPD == kSub) || (UPD == kGeneral && a.beta != 0.0);
+    const int sh0 = -7 * a.t;
     State R[CPT];
     long jc = 0;
     bool ok = true;
@@ -273,6 +305,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int row = tm * Cf::BM + row_t;
       const int col0 = tn * Cf::BN + half * CPT;
       const int e_row = row < a.M ? a.ea[row] : 0;
+      // column scales of this thread's CPT columns, one per lane (broadcast by shuffle)
+      int fcol[CPT / 32];
+#pragma unroll
+      for (int g = 0; g < CPT / 32; ++g) {
+        const int col = col0 + g * 32 + lane;
+        fcol[g] = col < a.N ? a.fb[col] : 0;
+      }
+      // pull this thread's C entries into L2 while the products run
+      if (needs_c && a.mode == 0 && row < a.M) {
+#pragma unroll 4
+        for (int c = 0; c < CPT; ++c)
+          if (col0 + c < a.N) prefetch_l2(a.C + row + (long)(col0 + c) * a.ldc);
+      }
 #pragma unroll
       for (int c = 0; c < CPT; ++c) R[c] = 0;
       int prevL = -1;
@@ -318,17 +363,23 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
               for (int jj = 0; jj < 8; ++jj) {
                 const int col = col0 + c8 * 8 + jj;
-                cv[jj] = (beta_mode != 0 && rowok && col < a.N) ? a.C[row + (long)col * a.ldc] : 0.0;
+                cv[jj] = (needs_c && rowok && col < a.N) ? a.C[row + (long)col * a.ldc] : 0.0;
               }
               tmem_ld_wait();
 #pragma unroll
               for (int jj = 0; jj < 8; ++jj) {
                 const int c = c8 * 8 + jj;
                 const int col = col0 + c;
+                const int f = __shfl_sync(0xFFFFFFFFu, fcol[c / 32], c % 32);
                 if (!rowok || col >= a.N || (a.lower && row < col)) continue;
-                const __int128 T = (__int128)R[c] * 128 + (__int128)f2i(r[jj]);
-                a.C[row + (long)col * a.ldc] =
-                    finish(a, T, e_row, col, alpha_mode, beta_mode, cv[jj]);
+                double D;
+                if (e_row == kNonFinite || f == kNonFinite)
+                  D = __longlong_as_double(0x7FF8000000000000ll);
+                else if (WIDE)
+                  D = rn_scaled((__int128)R[c] * 128 + (__int128)f2i(r[jj]), e_row + f + sh0);
+                else
+                  D = rn_scaled_r7((long long)R[c], f2i(r[jj]), e_row + f + sh0);
+                a.C[row + (long)col * a.ldc] = apply_update<UPD>(a, D, cv[jj]);
               }
             }
           } else {
@@ -361,14 +412,20 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int jj = 0; jj < 8; ++jj) {
             const int col = col0 + c8 * 8 + jj;
-            cv[jj] = (beta_mode != 0 && rowok && col < a.N) ? a.C[row + (long)col * a.ldc] : 0.0;
+            cv[jj] = (needs_c && rowok && col < a.N) ? a.C[row + (long)col * a.ldc] : 0.0;
           }
 #pragma unroll
           for (int jj = 0; jj < 8; ++jj) {
             const int c = c8 * 8 + jj;
             const int col = col0 + c;
+            const int f = __shfl_sync(0xFFFFFFFFu, fcol[c / 32], c % 32);
             if (!rowok || col >= a.N || (a.lower && row < col)) continue;
-            a.C[row + (long)col * a.ldc] = finish(a, (__int128)R[c], e_row, col, alpha_mode, beta_mode, cv[jj]);
+            double D;
+            if (e_row == kNonFinite || f == kNonFinite)
+              D = __longlong_as_double(0x7FF8000000000000ll);
+            else
+              D = rn_scaled((__int128)R[c], e_row + f + sh0);
+            a.C[row + (long)col * a.ldc] = apply_update<UPD>(a, D, cv[jj]);
           }
         }
       }
@@ -387,24 +444,33 @@ size_t gemm_stage_bytes(bool wide, int s) {
               : (size_t)s * (Cfg<false>::A_TILE + Cfg<false>::B_TILE);
 }
 
-cudaError_t launch_gemm(cudaStream_t st, bool wide, const CUtensorMap& tmA, const CUtensorMap& tmB,
-                        const GemmArgs& args, int grid, int stages, size_t smem_bytes) {
-  // The register hand-over between warpgroups is only valid if the block was
+template <bool WIDE, int UPD>
+cudaError_t launch_one(cudaStream_t st, const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& args, int grid,
+                       int stages, size_t smem_bytes) {
+  // The register hand-over between warpgroups is only valid if the block is
   // launched with exactly kLaunchRegs registers per thread.
   cudaFuncAttributes fa;
-  cudaError_t ea = cudaFuncGetAttributes(&fa, wide ? (const void*)gemm_kernel<true> : (const void*)gemm_kernel<false>);
-  if (ea != cudaSuccess) return ea;
+  cudaError_t e = cudaFuncGetAttributes(&fa, (const void*)gemm_kernel<WIDE, UPD>);
+  if (e != cudaSuccess) return e;
   if (fa.numRegs != kLaunchRegs) return cudaErrorInvalidConfiguration;
-  if (wide) {
-    cudaError_t e = cudaFuncSetAttribute(gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-    if (e != cudaSuccess) return e;
-    gemm_kernel<true><<<grid, kThreads, smem_bytes, st>>>(tmA, tmB, args, stages);
-  } else {
-    cudaError_t e = cudaFuncSetAttribute(gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-    if (e != cudaSuccess) return e;
-    gemm_kernel<false><<<grid, kThreads, smem_bytes, st>>>(tmA, tmB, args, stages);
-  }
+  e = cudaFuncSetAttribute(gemm_kernel<WIDE, UPD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+  if (e != cudaSuccess) return e;
+  gemm_kernel<WIDE, UPD><<<grid, kThreads, smem_bytes, st>>>(tmA, tmB, args, stages);
   return cudaGetLastError();
+}
+
+cudaError_t launch_gemm(cudaStream_t st, bool wide, const CUtensorMap& tmA, const CUtensorMap& tmB,
+                        const GemmArgs& args, int grid, int stages, size_t smem_bytes) {
+  const int upd = (args.alpha == -1.0 && args.beta == 1.0) ? kSub
+                  : (args.alpha == 1.0 && args.beta == 0.0) ? kSet : kGeneral;
+  if (wide) {
+    if (upd == kSub) return launch_one<true, kSub>(st, tmA, tmB, args, grid, stages, smem_bytes);
+    if (upd == kSet) return launch_one<true, kSet>(st, tmA, tmB, args, grid, stages, smem_bytes);
+    return launch_one<true, kGeneral>(st, tmA, tmB, args, grid, stages, smem_bytes);
+  }
+  if (upd == kSub) return launch_one<false, kSub>(st, tmA, tmB, args, grid, stages, smem_bytes);
+  if (upd == kSet) return launch_one<false, kSet>(st, tmA, tmB, args, grid, stages, smem_bytes);
+  return launch_one<false, kGeneral>(st, tmA, tmB, args, grid, stages, smem_bytes);
 }
 
 }  // namespace emul

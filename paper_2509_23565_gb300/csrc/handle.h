@@ -23,6 +23,15 @@ struct emul_handle_s {
   std::string last_error;
   void* encode_fn = nullptr;        // cuTensorMapEncodeTiled
   long long wait_limit = 2000000000LL;
+  // profiling (emul_profile_*)
+  long long launches = 0;
+  bool prof = false;
+  struct ProfRec {
+    cudaEvent_t e0, e1;
+    double flops, bytes;
+  };
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> event_pool;
 };
 
 namespace emul {

@@ -1,20 +1,643 @@
-// Factorization entry points (filled in below the product driver).
+// Blocked LU with partial pivoting and blocked Cholesky whose third-order work
+// runs through the emulated product (arXiv 2509.23565, Section 4, Eq. 5-7),
+// the triangular solves that use the factors, and the residual of Eq. 8.
+//
+// LU step (right-looking, block nb):
+//   1. panel [A11; A21] factored with partial pivoting: recursive halving; the
+//      inner Schur updates use the emulated product, the leaves (<= 32 columns)
+//      run a cooperative multi-block FP64 kernel (pivot search on the IEEE bit
+//      patterns, one bounded grid barrier per column);
+//   2. the panel's row interchanges applied to the columns left and right of it;
+//   3. U12 = L11^-1 A12: L11^-1 formed in FP64 (unit lower, nb x nb), the
+//      product by the emulated GEMM;
+//   4. A22 <- A22 - L21 U12 by the emulated GEMM (alpha = -1, beta = 1).
+// Cholesky step (lower): FP64 diagonal block, L21 = A21 L11^-T through an FP64
+// L11^-1 and the emulated GEMM, then A22 <- A22 - L21 L21^T on lower tiles only,
+// with one slice set serving both operands.
+#include <cmath>
+#include <cstdio>
+
+#include <cuda_runtime.h>
+
 #include "handle.h"
 
+namespace emul {
+
+namespace {
+
+constexpr int kLeaf = 32;           // widest panel handled by the leaf kernel
+constexpr int kLeafThreads = 256;
+constexpr int kStatusTimeout = -4;
+constexpr size_t kAl = 256;
+inline size_t al(size_t x) { return (x + kAl - 1) / kAl * kAl; }
+
+struct GridBar {
+  unsigned count;
+  unsigned gen;
+};
+
+// Bounded grid-wide barrier for a cooperative launch of G blocks.
+__device__ bool grid_sync(GridBar* gb, unsigned G, long long limit, int* status) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &gb->gen;
+    const unsigned g = *vgen;
+    __threadfence();
+    bool ok = true;
+    if (atomicAdd(&gb->count, 1u) == G - 1) {
+      atomicExch(&gb->count, 0u);
+      __threadfence();
+      atomicAdd(&gb->gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == g) {
+        if (clock64() - t0 > limit) {
+          ok = false;
+          atomicExch(status, kStatusTimeout);
+          break;
+        }
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+__device__ __forceinline__ uint64_t absbits(double x) {
+  return static_cast<uint64_t>(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// (value, row) pair ordering of the pivot search: larger |value| wins, ties
+// go to the smaller row (the first maximal index, as LAPACK's idamax).
+__device__ __forceinline__ bool better(uint64_t v1, int r1, uint64_t v2, int r2) {
+  return v1 > v2 || (v1 == v2 && r1 < r2);
+}
+
+// Leaf panel: rows d0..n-1, columns d0..d0+w-1 of A, factored in place with
+// partial pivoting.  Block b keeps panel rows [b*R, b*R+R) in shared memory.
+__global__ void __launch_bounds__(kLeafThreads) getf2_leaf_kernel(double* A, long lda, int n, int d0, int w, int R,
+                                                                 int32_t* ipiv, int32_t* info, GridBar* gb,
+                                                                 double* cand_rows, uint64_t* cand_val,
+                                                                 int* cand_idx, double* diag_rows, int* status,
+                                                                 long long limit) {
+  extern __shared__ double P[];   // P[c*R + lr]
+  __shared__ double prow[kLeaf], crow[kLeaf];
+  __shared__ uint64_t red_v[kLeafThreads / 32];
+  __shared__ int red_r[kLeafThreads / 32];
+  __shared__ int win_s;
+  const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+  const int mp = n - d0;
+  const int r0 = b * R;
+  const int rcount = mp - r0 < R ? (mp - r0 > 0 ? mp - r0 : 0) : R;
+  for (int c = 0; c < w; ++c)
+    for (int lr = tid; lr < rcount; lr += blockDim.x) P[c * R + lr] = A[(d0 + r0 + lr) + static_cast<long>(d0 + c) * lda];
+  __syncthreads();
+
+  for (int c = 0; c < w; ++c) {
+    const int par = c & 1;
+    // (a) local candidate for column c over own rows with panel row >= c
+    uint64_t bv = 0;
+    int br = 0x7FFFFFFF;
+    for (int lr = tid; lr < rcount; lr += blockDim.x) {
+      const int pr = r0 + lr;
+      if (pr < c) continue;
+      const uint64_t v = absbits(P[c * R + lr]);
+      if (better(v, pr, bv, br)) {
+        bv = v;
+        br = pr;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t v2 = __shfl_xor_sync(0xFFFFFFFFu, bv, o);
+      const int r2 = __shfl_xor_sync(0xFFFFFFFFu, br, o);
+      if (better(v2, r2, bv, br)) {
+        bv = v2;
+        br = r2;
+      }
+    }
+    if ((tid & 31) == 0) {
+      red_v[tid >> 5] = bv;
+      red_r[tid >> 5] = br;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      for (int i = 1; i < static_cast<int>(blockDim.x / 32); ++i)
+        if (better(red_v[i], red_r[i], bv, br)) {
+          bv = red_v[i];
+          br = red_r[i];
+        }
+      cand_val[par * G + b] = bv;
+      cand_idx[par * G + b] = br;
+      win_s = br;
+    }
+    __syncthreads();
+    {
+      const int pr = win_s;
+      if (pr != 0x7FFFFFFF)
+        for (int cc = tid; cc < w; cc += blockDim.x) cand_rows[(static_cast<long>(par) * G + b) * kLeaf + cc] = P[cc * R + (pr - r0)];
+      if (c >= r0 && c < r0 + rcount)
+        for (int cc = tid; cc < w; cc += blockDim.x) diag_rows[par * kLeaf + cc] = P[cc * R + (c - r0)];
+    }
+    // (b) one barrier per column
+    if (!grid_sync(gb, G, limit, status)) return;
+    // (c) global pivot
+    if (tid == 0) {
+      uint64_t gv = 0;
+      int gr = 0x7FFFFFFF, gb_ = 0;
+      volatile uint64_t* cv = cand_val;
+      volatile int* ci = cand_idx;
+      for (int i = 0; i < G; ++i) {
+        const uint64_t v = cv[par * G + i];
+        const int r = ci[par * G + i];
+        if (r != 0x7FFFFFFF && better(v, r, gv, gr)) {
+          gv = v;
+          gr = r;
+          gb_ = i;
+        }
+      }
+      win_s = gr;
+      red_r[0] = gb_;
+      if (b == 0) {
+        ipiv[d0 + c] = d0 + gr + 1;
+        if (gv == 0) atomicCAS(info, 0, d0 + c + 1);
+      }
+    }
+    __syncthreads();
+    const int p = win_s;
+    const int pb = red_r[0];
+    for (int cc = tid; cc < w; cc += blockDim.x) {
+      prow[cc] = static_cast<volatile double*>(cand_rows)[(static_cast<long>(par) * G + pb) * kLeaf + cc];
+      crow[cc] = static_cast<volatile double*>(diag_rows)[par * kLeaf + cc];
+    }
+    __syncthreads();
+    const double piv = prow[c];
+    if (piv != 0.0) {
+      if (p != c) {
+        if (c >= r0 && c < r0 + rcount)
+          for (int cc = tid; cc < w; cc += blockDim.x) P[cc * R + (c - r0)] = prow[cc];
+        if (p >= r0 && p < r0 + rcount)
+          for (int cc = tid; cc < w; cc += blockDim.x) P[cc * R + (p - r0)] = crow[cc];
+      }
+      __syncthreads();
+      const bool use_rcp = fabs(piv) >= 2.2250738585072014e-308;
+      const double rcp = 1.0 / piv;
+      for (int lr = tid; lr < rcount; lr += blockDim.x) {
+        const int pr = r0 + lr;
+        if (pr <= c) continue;
+        const double l = use_rcp ? P[c * R + lr] * rcp : P[c * R + lr] / piv;
+        P[c * R + lr] = l;
+        for (int cc = c + 1; cc < w; ++cc) P[cc * R + lr] = fma(-l, prow[cc], P[cc * R + lr]);
+      }
+    }
+    __syncthreads();
+  }
+  for (int c = 0; c < w; ++c)
+    for (int lr = tid; lr < rcount; lr += blockDim.x) A[(d0 + r0 + lr) + static_cast<long>(d0 + c) * lda] = P[c * R + lr];
+}
+
+// Row interchanges ipiv[k1..k2) (1-based global rows) applied to columns [c0, c1).
+__global__ void laswp_kernel(double* A, long lda, int c0, int c1, const int32_t* ipiv, int k1, int k2) {
+  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= c1) return;
+  double* col = A + static_cast<long>(c) * lda;
+  for (int k = k1; k < k2; ++k) {
+    const int p = ipiv[k] - 1;
+    if (p != k) {
+      const double t = col[k];
+      col[k] = col[p];
+      col[p] = t;
+    }
+  }
+}
+
+// X (w1 x w2 at A[d0.., c0..]) <- L^-1 X with L unit lower w1 x w1 at A[d0.., d0..].
+__global__ void trsm_small_kernel(double* A, long lda, int d0, int w1, int c0) {
+  __shared__ double x[128];
+  const int j = c0 + blockIdx.x, i = threadIdx.x;
+  double* col = A + static_cast<long>(j) * lda + d0;
+  if (i < w1) x[i] = col[i];
+  __syncthreads();
+  for (int k = 0; k < w1; ++k) {
+    if (i > k && i < w1) x[i] = fma(-A[(d0 + i) + static_cast<long>(d0 + k) * lda], x[k], x[i]);
+    __syncthreads();
+  }
+  if (i < w1) col[i] = x[i];
+}
+
+// inv (nb x nb, ld nb) <- L^-1 for L = the nb x nb lower triangle at A[d0.., d0..]
+// (unit diagonal if `unit`).  One block per column of the inverse.
+__global__ void trtri_lower_kernel(const double* A, long lda, int d0, int nb, int unit, double* inv) {
+  extern __shared__ double xs[];
+  const int j = blockIdx.x, i = threadIdx.x;
+  const double* L = A + d0 + static_cast<long>(d0) * lda;
+  if (i < nb) xs[i] = (i == j) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int k = j; k < nb; ++k) {
+    if (!unit) {
+      if (i == k) xs[k] = xs[k] / L[k + static_cast<long>(k) * lda];
+      __syncthreads();
+    }
+    const double xk = xs[k];
+    if (i > k && i < nb) xs[i] = fma(-L[i + static_cast<long>(k) * lda], xk, xs[i]);
+    __syncthreads();
+  }
+  if (i < nb) inv[i + static_cast<long>(j) * nb] = (i < j) ? 0.0 : xs[i];
+}
+
+// Unblocked lower Cholesky of the nb x nb diagonal block at A[d0.., d0..] (one block).
+__global__ void potf2_kernel(double* A, long lda, int d0, int nb, int32_t* info) {
+  double* D = A + d0 + static_cast<long>(d0) * lda;
+  __shared__ double djj;
+  __shared__ int fail;
+  const int i = threadIdx.x;
+  if (i == 0) fail = (*info != 0);
+  __syncthreads();
+  if (fail) return;
+  for (int j = 0; j < nb; ++j) {
+    if (i == 0) {
+      const double d = D[j + static_cast<long>(j) * lda];
+      if (!(d > 0.0)) {
+        atomicCAS(info, 0, d0 + j + 1);
+        fail = 1;
+      } else {
+        djj = sqrt(d);
+        D[j + static_cast<long>(j) * lda] = djj;
+      }
+    }
+    __syncthreads();
+    if (fail) return;
+    const double r = 1.0 / djj;
+    for (int ii = j + 1 + i; ii < nb; ii += blockDim.x) D[ii + static_cast<long>(j) * lda] *= r;
+    __syncthreads();
+    for (int ii = j + 1 + i; ii < nb; ii += blockDim.x) {
+      const double lij = D[ii + static_cast<long>(j) * lda];
+      for (int kk = j + 1; kk <= ii; ++kk)
+        D[ii + static_cast<long>(kk) * lda] = fma(-lij, D[kk + static_cast<long>(j) * lda], D[ii + static_cast<long>(kk) * lda]);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ solves
+// x[d0 .. d0+bs) of every right-hand side solved with the bs x bs diagonal block
+// of a triangular matrix T (lower / upper, unit / non-unit; `trans`: use T^T
+// where T is stored lower).  One block per right-hand side.
+__global__ void trsv_block_kernel(const double* T, long ldt, double* X, long ldx, int d0, int bs, int lower, int unit,
+                                  int trans) {
+  __shared__ double x[128];
+  double* xc = X + static_cast<long>(blockIdx.x) * ldx + d0;
+  const int i = threadIdx.x;
+  if (i < bs) x[i] = xc[i];
+  __syncthreads();
+  auto t = [&](int r, int c) -> double {
+    return trans ? T[(d0 + c) + static_cast<long>(d0 + r) * ldt] : T[(d0 + r) + static_cast<long>(d0 + c) * ldt];
+  };
+  if (lower) {
+    for (int k = 0; k < bs; ++k) {
+      if (!unit && i == k) x[k] = x[k] / t(k, k);
+      __syncthreads();
+      if (i > k && i < bs) x[i] = fma(-t(i, k), x[k], x[i]);
+      __syncthreads();
+    }
+  } else {
+    for (int k = bs - 1; k >= 0; --k) {
+      if (!unit && i == k) x[k] = x[k] / t(k, k);
+      __syncthreads();
+      if (i < k) x[i] = fma(-t(i, k), x[k], x[i]);
+      __syncthreads();
+    }
+  }
+  if (i < bs) xc[i] = x[i];
+}
+
+// x[r] -= sum_{c in [c0, c0+bs)} T(r, c) x[c] for rows r in [r0, r1); T(r, c) =
+// T[r + c*ldt] or, with `trans`, T[c + r*ldt].  blockIdx.y = right-hand side.
+__global__ void gemv_update_kernel(const double* T, long ldt, double* X, long ldx, int r0, int r1, int c0, int bs,
+                                   int trans) {
+  __shared__ double xs[128];
+  double* xc = X + static_cast<long>(blockIdx.y) * ldx;
+  if (threadIdx.x < bs) xs[threadIdx.x] = xc[c0 + threadIdx.x];
+  __syncthreads();
+  if (!trans) {
+    const int r = r0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= r1) return;
+    double acc = 0.0;
+    for (int c = 0; c < bs; ++c) acc = fma(T[r + static_cast<long>(c0 + c) * ldt], xs[c], acc);
+    xc[r] -= acc;
+  } else {
+    // one warp per row: contiguous reads of T[c0.., r]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = r0 + blockIdx.x * (blockDim.x / 32) + warp;
+    if (r >= r1) return;
+    double acc = 0.0;
+    for (int c = lane; c < bs; c += 32) acc = fma(T[(c0 + c) + static_cast<long>(r) * ldt], xs[c], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if (lane == 0) xc[r] -= acc;
+  }
+}
+
+// Residual pass of Eq. 8: per row, r_i = sum_j a_ij x_j - b_i and sum_j |a_ij|;
+// maxima of |r_i| and of the row sums collected with atomicMax on the bits.
+__global__ void residual_kernel(int n, const double* A, long lda, const double* x, const double* b,
+                                unsigned long long* acc) {
+  extern __shared__ double xs[];
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  double s = 0.0, sa = 0.0;
+  for (int c0 = 0; c0 < n; c0 += 2048) {
+    const int cn = n - c0 < 2048 ? n - c0 : 2048;
+    __syncthreads();
+    for (int i = threadIdx.x; i < cn; i += blockDim.x) xs[i] = x[c0 + i];
+    __syncthreads();
+    if (r < n)
+      for (int c = 0; c < cn; ++c) {
+        const double a = A[r + static_cast<long>(c0 + c) * lda];
+        s = fma(a, xs[c], s);
+        sa += fabs(a);
+      }
+  }
+  if (r < n) {
+    const double res = fabs(s - b[r]);
+    atomicMax(&acc[0], static_cast<unsigned long long>(__double_as_longlong(res)));
+    atomicMax(&acc[1], static_cast<unsigned long long>(__double_as_longlong(sa)));
+    atomicMax(&acc[2], static_cast<unsigned long long>(__double_as_longlong(fabs(x[r]))));
+    atomicMax(&acc[3], static_cast<unsigned long long>(__double_as_longlong(fabs(b[r]))));
+  }
+}
+
+__global__ void residual_finish_kernel(int n, const unsigned long long* acc, double* out) {
+  const double r = __longlong_as_double(static_cast<long long>(acc[0]));
+  const double an = __longlong_as_double(static_cast<long long>(acc[1]));
+  const double xn = __longlong_as_double(static_cast<long long>(acc[2]));
+  const double bn = __longlong_as_double(static_cast<long long>(acc[3]));
+  const double eps = 1.1102230246251565e-16;   // 2^-53
+  out[0] = r / ((an * xn + bn) * n * eps);
+  out[1] = r / (an * xn * n * eps);
+}
+
+// ------------------------------------------------------------------ host helpers
+struct LuBufs {
+  double* inv;          // nb x nb
+  double* cand_rows;    // [2][G][kLeaf]
+  uint64_t* cand_val;   // [2][G]
+  int* cand_idx;        // [2][G]
+  double* diag_rows;    // [2][kLeaf]
+  GridBar* bar;
+  unsigned long long* racc;
+};
+
+size_t lu_extra_bytes(int nb, int nsm) {
+  return al(static_cast<size_t>(nb) * nb * 8) + al(2ull * nsm * kLeaf * 8) + al(2ull * nsm * 8) + al(2ull * nsm * 4) +
+         al(2ull * kLeaf * 8) + al(sizeof(GridBar)) + al(4 * 8) + kAl;
+}
+
+LuBufs carve(emul_handle_t h, size_t off, int nb) {
+  uint8_t* p = static_cast<uint8_t*>(h->ws) + al(off);
+  LuBufs b;
+  b.inv = reinterpret_cast<double*>(p);
+  p += al(static_cast<size_t>(nb) * nb * 8);
+  b.cand_rows = reinterpret_cast<double*>(p);
+  p += al(2ull * h->nsm * kLeaf * 8);
+  b.cand_val = reinterpret_cast<uint64_t*>(p);
+  p += al(2ull * h->nsm * 8);
+  b.cand_idx = reinterpret_cast<int*>(p);
+  p += al(2ull * h->nsm * 4);
+  b.diag_rows = reinterpret_cast<double*>(p);
+  p += al(2ull * kLeaf * 8);
+  b.bar = reinterpret_cast<GridBar*>(p);
+  p += al(sizeof(GridBar));
+  b.racc = reinterpret_cast<unsigned long long*>(p);
+  return b;
+}
+
+int launch_leaf(emul_handle_t h, double* A, long lda, int n, int d0, int w, int32_t* ipiv, int32_t* info,
+                const LuBufs& B) {
+  const int mp = n - d0;
+  int G = (mp + 511) / 512;
+  const int smem_rows_cap = 200 * 1024 / (w * 8);
+  if ((mp + G - 1) / G > smem_rows_cap) G = (mp + smem_rows_cap - 1) / smem_rows_cap;
+  if (G < 1) G = 1;
+  if (G > h->nsm) G = h->nsm;
+  const int R = (mp + G - 1) / G;
+  const size_t smem = static_cast<size_t>(R) * w * 8;
+  if (smem > 220 * 1024) return set_error(h, EMUL_NOT_SUPPORTED, "panel too tall for the leaf kernel");
+  int rc = check_cuda(h, cudaMemsetAsync(B.bar, 0, sizeof(GridBar), h->stream), "barrier reset");
+  if (rc) return rc;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(getf2_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    attr_set = true;
+  }
+  long long limit = h->wait_limit;
+  int* status = h->d_status;
+  void* args[] = {&A, const_cast<long*>(&lda), &n, &d0, &w, const_cast<int*>(&R), &ipiv, &info,
+                  const_cast<GridBar**>(&B.bar), const_cast<double**>(&B.cand_rows), const_cast<uint64_t**>(&B.cand_val),
+                  const_cast<int**>(&B.cand_idx), const_cast<double**>(&B.diag_rows), &status, &limit};
+  h->launches++;
+  return check_cuda(h,
+                    cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(getf2_leaf_kernel), dim3(G),
+                                                dim3(kLeafThreads), args, smem, h->stream),
+                    "panel leaf");
+}
+
+int laswp(emul_handle_t h, double* A, long lda, int c0, int c1, const int32_t* ipiv, int k1, int k2) {
+  if (c1 <= c0 || k2 <= k1) return EMUL_OK;
+  laswp_kernel<<<(c1 - c0 + 127) / 128, 128, 0, h->stream>>>(A, lda, c0, c1, ipiv, k1, k2);
+  h->launches++;
+  return check_cuda(h, cudaGetLastError(), "laswp");
+}
+
+// Recursive panel factorization of rows d0..n-1, columns d0..d0+w-1.
+int rgetrf(emul_handle_t h, double* A, long lda, int n, int d0, int w, int32_t* ipiv, int32_t* info, int s,
+           const LuBufs& B) {
+  if (w <= kLeaf) return launch_leaf(h, A, lda, n, d0, w, ipiv, info, B);
+  const int w1 = (w / 2 + 7) / 8 * 8;
+  const int w2 = w - w1;
+  int rc = rgetrf(h, A, lda, n, d0, w1, ipiv, info, s, B);
+  if (rc) return rc;
+  rc = laswp(h, A, lda, d0 + w1, d0 + w, ipiv, d0, d0 + w1);
+  if (rc) return rc;
+  trsm_small_kernel<<<w2, 128, 0, h->stream>>>(A, lda, d0, w1, d0 + w1);
+  h->launches++;
+  rc = check_cuda(h, cudaGetLastError(), "panel trsm");
+  if (rc) return rc;
+  const int m2 = n - d0 - w1;
+  // A22 (m2 x w2) -= A21 (m2 x w1) * A12 (w1 x w2)
+  rc = gemm_run(h, m2, w2, w1, -1.0, Operand{A + (d0 + w1) + static_cast<long>(d0) * lda, 1, lda},
+                Operand{A + d0 + static_cast<long>(d0 + w1) * lda, lda, 1}, 1.0,
+                A + (d0 + w1) + static_cast<long>(d0 + w1) * lda, lda, s, false, 0, nullptr, 0, 0);
+  if (rc) return rc;
+  rc = rgetrf(h, A, lda, n, d0 + w1, w2, ipiv, info, s, B);
+  if (rc) return rc;
+  return laswp(h, A, lda, d0, d0 + w1, ipiv, d0 + w1, d0 + w);
+}
+
+}  // namespace
+
+}  // namespace emul
+
+using emul::Operand;
+
 extern "C" {
-int emul_dgetrf(emul_handle_t h, int, double*, int, int32_t*, int, int, int32_t*, emul_stats*) {
-  return emul::set_error(h, EMUL_NOT_SUPPORTED, "not built yet");
+
+int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int nb, int slices, int32_t* info,
+                emul_stats* stats) {
+  if (!h) return EMUL_INVALID_ARG;
+  if (nb == 0) nb = 128;
+  if (n < 0 || lda < (n > 1 ? n : 1) || nb < 16 || nb > 256 || nb % 16 != 0 || slices < 1 ||
+      slices > emul::kMaxSlices || (n > 0 && (!A || !ipiv || !info)))
+    return emul::set_error(h, EMUL_INVALID_ARG, "emul_dgetrf: invalid argument");
+  if (stats) *stats = emul_stats{0, slices, slices, 0, 0.0};
+  if (n == 0) return EMUL_OK;
+  int rc = emul::check_cuda(h, cudaMemsetAsync(info, 0, sizeof(int32_t), h->stream), "info reset");
+  if (rc) return rc;
+  const size_t gw = emul::gemm_workspace_bytes(n, n, nb, slices, false);
+  rc = emul::reserve_workspace(h, gw + emul::lu_extra_bytes(nb, h->nsm));
+  if (rc) return rc;
+  const emul::LuBufs B = emul::carve(h, gw, nb);
+  for (int j0 = 0; j0 < n; j0 += nb) {
+    const int jb = nb < n - j0 ? nb : n - j0;
+    rc = emul::rgetrf(h, A, lda, n, j0, jb, ipiv, info, slices, B);
+    if (rc) return rc;
+    rc = emul::laswp(h, A, lda, 0, j0, ipiv, j0, j0 + jb);
+    if (rc) return rc;
+    rc = emul::laswp(h, A, lda, j0 + jb, n, ipiv, j0, j0 + jb);
+    if (rc) return rc;
+    const int m2 = n - j0 - jb;
+    if (m2 > 0) {
+      emul::trtri_lower_kernel<<<jb, (jb + 31) / 32 * 32, jb * sizeof(double), h->stream>>>(A, lda, j0, jb, 1, B.inv);
+      h->launches++;
+      rc = emul::check_cuda(h, cudaGetLastError(), "trtri");
+      if (rc) return rc;
+      double* A12 = A + j0 + static_cast<long>(j0 + jb) * lda;
+      // U12 = L11^-1 A12 (jb x m2), written over A12
+      rc = emul::gemm_run(h, jb, m2, jb, 1.0, Operand{B.inv, 1, jb}, Operand{A12, lda, 1}, 0.0, A12, lda, slices,
+                          false, 0, nullptr, 0, 0);
+      if (rc) return rc;
+      // A22 -= L21 U12
+      rc = emul::gemm_run(h, m2, m2, jb, -1.0, Operand{A + (j0 + jb) + static_cast<long>(j0) * lda, 1, lda},
+                          Operand{A12, lda, 1}, 1.0, A + (j0 + jb) + static_cast<long>(j0 + jb) * lda, lda, slices,
+                          false, 0, nullptr, 0, 0);
+      if (rc) return rc;
+    }
+    if (stats) stats->steps++;
+  }
+  return EMUL_OK;
 }
-int emul_dgetrs(emul_handle_t h, int, int, const double*, int, const int32_t*, double*, int) {
-  return emul::set_error(h, EMUL_NOT_SUPPORTED, "not built yet");
+
+int emul_dgetrs(emul_handle_t h, int n, int nrhs, const double* LU, int lda, const int32_t* ipiv, double* B,
+                int ldb) {
+  if (!h) return EMUL_INVALID_ARG;
+  if (n < 0 || nrhs < 0 || lda < (n > 1 ? n : 1) || ldb < (n > 1 ? n : 1) || (n > 0 && nrhs > 0 && (!LU || !ipiv || !B)))
+    return emul::set_error(h, EMUL_INVALID_ARG, "emul_dgetrs: invalid argument");
+  if (n == 0 || nrhs == 0) return EMUL_OK;
+  int rc = emul::laswp(h, B, ldb, 0, nrhs, ipiv, 0, n);
+  if (rc) return rc;
+  constexpr int bs = 128;  // diagonal blocks of the substitution
+  for (int d0 = 0; d0 < n; d0 += bs) {
+    const int b = bs < n - d0 ? bs : n - d0;
+    emul::trsv_block_kernel<<<nrhs, 128, 0, h->stream>>>(LU, lda, B, ldb, d0, b, 1, 1, 0);
+    h->launches += (d0 + b < n) ? 2 : 1;
+    if (d0 + b < n)
+      emul::gemv_update_kernel<<<dim3((n - d0 - b + 255) / 256, nrhs), 256, 0, h->stream>>>(LU, lda, B, ldb, d0 + b,
+                                                                                               n, d0, b, 0);
+  }
+  for (int d0 = ((n - 1) / bs) * bs; d0 >= 0; d0 -= bs) {
+    const int b = bs < n - d0 ? bs : n - d0;
+    emul::trsv_block_kernel<<<nrhs, 128, 0, h->stream>>>(LU, lda, B, ldb, d0, b, 0, 0, 0);
+    h->launches += (d0 > 0) ? 2 : 1;
+    if (d0 > 0)
+      emul::gemv_update_kernel<<<dim3((d0 + 255) / 256, nrhs), 256, 0, h->stream>>>(LU, lda, B, ldb, 0, d0, d0, b, 0);
+  }
+  return emul::check_cuda(h, cudaGetLastError(), "getrs");
 }
-int emul_dpotrf(emul_handle_t h, char, int, double*, int, int, int, int32_t*, emul_stats*) {
-  return emul::set_error(h, EMUL_NOT_SUPPORTED, "not built yet");
+
+int emul_dpotrf(emul_handle_t h, char uplo, int n, double* A, int lda, int nb, int slices, int32_t* info,
+                emul_stats* stats) {
+  if (!h) return EMUL_INVALID_ARG;
+  if (nb == 0) nb = 128;
+  if ((uplo != 'L' && uplo != 'l') || n < 0 || lda < (n > 1 ? n : 1) || nb < 16 || nb > 256 || nb % 16 != 0 ||
+      slices < 1 || slices > emul::kMaxSlices || (n > 0 && (!A || !info)))
+    return emul::set_error(h, EMUL_INVALID_ARG, "emul_dpotrf: invalid argument");
+  if (stats) *stats = emul_stats{0, slices, slices, 0, 0.0};
+  if (n == 0) return EMUL_OK;
+  int rc = emul::check_cuda(h, cudaMemsetAsync(info, 0, sizeof(int32_t), h->stream), "info reset");
+  if (rc) return rc;
+  const size_t gw = emul::gemm_workspace_bytes(n, n, nb, slices, false);
+  rc = emul::reserve_workspace(h, gw + emul::lu_extra_bytes(nb, h->nsm));
+  if (rc) return rc;
+  const emul::LuBufs B = emul::carve(h, gw, nb);
+  for (int j0 = 0; j0 < n; j0 += nb) {
+    const int jb = nb < n - j0 ? nb : n - j0;
+    emul::potf2_kernel<<<1, 256, 0, h->stream>>>(A, lda, j0, jb, info);
+    h->launches++;
+    rc = emul::check_cuda(h, cudaGetLastError(), "potf2");
+    if (rc) return rc;
+    const int m2 = n - j0 - jb;
+    if (m2 > 0) {
+      emul::trtri_lower_kernel<<<jb, (jb + 31) / 32 * 32, jb * sizeof(double), h->stream>>>(A, lda, j0, jb, 0, B.inv);
+      h->launches++;
+      rc = emul::check_cuda(h, cudaGetLastError(), "trtri");
+      if (rc) return rc;
+      double* A21 = A + (j0 + jb) + static_cast<long>(j0) * lda;
+      // L21 = A21 L11^-T: operand B is (L11^-1)^T, whose row j is row j of L11^-1
+      rc = emul::gemm_run(h, m2, jb, jb, 1.0, Operand{A21, 1, lda}, Operand{B.inv, 1, jb}, 0.0, A21, lda, slices,
+                          false, 0, nullptr, 0, 0);
+      if (rc) return rc;
+      // A22 -= L21 L21^T on the lower triangle; one slice set for both operands
+      rc = emul::gemm_run(h, m2, m2, jb, -1.0, Operand{A21, 1, lda}, Operand{A21, 1, lda}, 1.0,
+                          A + (j0 + jb) + static_cast<long>(j0 + jb) * lda, lda, slices, true, 0, nullptr, 0, 0);
+      if (rc) return rc;
+    }
+    if (stats) stats->steps++;
+  }
+  return EMUL_OK;
 }
-int emul_dpotrs(emul_handle_t h, char, int, int, const double*, int, double*, int) {
-  return emul::set_error(h, EMUL_NOT_SUPPORTED, "not built yet");
+
+int emul_dpotrs(emul_handle_t h, char uplo, int n, int nrhs, const double* L, int lda, double* B, int ldb) {
+  if (!h) return EMUL_INVALID_ARG;
+  if ((uplo != 'L' && uplo != 'l') || n < 0 || nrhs < 0 || lda < (n > 1 ? n : 1) || ldb < (n > 1 ? n : 1) ||
+      (n > 0 && nrhs > 0 && (!L || !B)))
+    return emul::set_error(h, EMUL_INVALID_ARG, "emul_dpotrs: invalid argument");
+  if (n == 0 || nrhs == 0) return EMUL_OK;
+  constexpr int bs = 128;
+  for (int d0 = 0; d0 < n; d0 += bs) {
+    const int b = bs < n - d0 ? bs : n - d0;
+    emul::trsv_block_kernel<<<nrhs, 128, 0, h->stream>>>(L, lda, B, ldb, d0, b, 1, 0, 0);
+    h->launches += (d0 + b < n) ? 2 : 1;
+    if (d0 + b < n)
+      emul::gemv_update_kernel<<<dim3((n - d0 - b + 255) / 256, nrhs), 256, 0, h->stream>>>(L, lda, B, ldb, d0 + b,
+                                                                                               n, d0, b, 0);
+  }
+  for (int d0 = ((n - 1) / bs) * bs; d0 >= 0; d0 -= bs) {
+    const int b = bs < n - d0 ? bs : n - d0;
+    emul::trsv_block_kernel<<<nrhs, 128, 0, h->stream>>>(L, lda, B, ldb, d0, b, 0, 0, 1);
+    h->launches += (d0 > 0) ? 2 : 1;
+    if (d0 > 0)
+      emul::gemv_update_kernel<<<dim3((d0 + 7) / 8, nrhs), 256, 0, h->stream>>>(L, lda, B, ldb, 0, d0, d0, b, 1);
+  }
+  return emul::check_cuda(h, cudaGetLastError(), "potrs");
 }
-int emul_backward_error(emul_handle_t h, int, const double*, int, const double*, const double*, double*) {
-  return emul::set_error(h, EMUL_NOT_SUPPORTED, "not built yet");
+
+int emul_backward_error(emul_handle_t h, int n, const double* A, int lda, const double* x, const double* b,
+                        double* out) {
+  if (!h) return EMUL_INVALID_ARG;
+  if (n <= 0 || lda < n || !A || !x || !b || !out)
+    return emul::set_error(h, EMUL_INVALID_ARG, "emul_backward_error: invalid argument");
+  const size_t need = emul::lu_extra_bytes(16, h->nsm);
+  int rc = emul::reserve_workspace(h, need);
+  if (rc) return rc;
+  const emul::LuBufs B = emul::carve(h, 0, 16);
+  rc = emul::check_cuda(h, cudaMemsetAsync(B.racc, 0, 4 * sizeof(unsigned long long), h->stream), "residual reset");
+  if (rc) return rc;
+  emul::residual_kernel<<<(n + 255) / 256, 256, 2048 * sizeof(double), h->stream>>>(n, A, lda, x, b, B.racc);
+  h->launches += 2;
+  emul::residual_finish_kernel<<<1, 1, 0, h->stream>>>(n, B.racc, out);
+  return emul::check_cuda(h, cudaGetLastError(), "residual");
 }
-}
+
+}  // extern "C"

@@ -1,0 +1,186 @@
+"""GPU LU / Cholesky / solves through the C-ABI, checked against the oracle.
+
+Pivot order may legitimately differ between the emulated and the FP64
+factorization (Section 4: only the Schur update is emulated, but its low-order
+bits steer later pivot choices), so factorizations are compared through what is
+unique: the factorization residual, the Eq. 8 scaled residual and backward
+error of the solve (computed by the oracle on the CPU), exact results on
+small-integer matrices (where every emulated product is exact), the info
+index of singular / non-SPD inputs, and valid pivot vectors.
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import lu as olu, residual
+from paper_2509_23565_gb300 import inputs
+from paper_2509_23565_gb300.binding import ColMajor
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _factor(gpu_lib, A, nb, s, ld=None):
+    dA = ColMajor.from_numpy(A, ld=ld)
+    ipiv, info = gpu_lib.dgetrf(dA, nb=nb, slices=s)
+    gpu_lib.sync_status()
+    return dA, ipiv, int(info.item())
+
+
+def _valid_ipiv(ipiv, n):
+    p = ipiv.cpu().numpy()
+    return p.shape == (n,) and (p >= np.arange(1, n + 1)).all() and (p <= n).all()
+
+
+@pytest.mark.parametrize("n,nb", [(1, 64), (5, 16), (100, 32), (257, 64), (700, 128), (1024, 64)])
+@pytest.mark.parametrize("s", [7, 8])
+def test_getrf_getrs_uniform(gpu_lib, n, nb, s):
+    A = inputs.uniform(n, n, seed=10 + n)
+    b = inputs.vector(n, seed=20 + n)
+    dA, ipiv, info = _factor(gpu_lib, A, nb, s, ld=n + 2)
+    assert info == 0 and _valid_ipiv(ipiv, n)
+    LU = dA.numpy()
+    # s = 8 reaches FP64-level factors; at s = 7 each emulated update carries
+    # about 2^-42 k of relative error, so the factor residual is O(10) (the
+    # oracle's emulated LU gives 12.6 at n = 257), while the solve still passes
+    assert residual.lu_residual(A, LU, ipiv.cpu().numpy()) < (16 if s == 8 else 100)
+    db = ColMajor.from_numpy(b)
+    gpu_lib.dgetrs(dA, ipiv, db)
+    gpu_lib.sync_status()
+    x = db.numpy()[:, 0]
+    assert residual.scaled_residual(A, x, b) < 16
+    assert residual.backward_error(A, x, b) < 16
+    # the device residual kernel agrees with the oracle's formula
+    out = gpu_lib.backward_error(ColMajor.from_numpy(A), db, ColMajor.from_numpy(b)).cpu().numpy()
+    assert abs(out[0] - residual.scaled_residual(A, x, b)) <= 1e-9 * max(1.0, out[0])
+    assert abs(out[1] - residual.backward_error(A, x, b)) <= 1e-9 * max(1.0, out[1])
+
+
+@pytest.mark.parametrize("r", [4, 8, 16])
+def test_getrf_log_scaled(gpu_lib, r):
+    n = 512
+    A = inputs.log_scaled(n, n, r, seed=30 + r)
+    b = inputs.vector(n, seed=31)
+    dA, ipiv, info = _factor(gpu_lib, A, 64, 8)
+    assert info == 0
+    db = ColMajor.from_numpy(b)
+    gpu_lib.dgetrs(dA, ipiv, db)
+    x = db.numpy()[:, 0]
+    assert residual.backward_error(A, x, b) < 16
+
+
+def test_emulation_quality_tracks_oracle(gpu_lib):
+    """Same method on both sides: the GPU and oracle emulated LU give backward
+    errors of the same order at every slice count (3 fails, 8 passes)."""
+    n = 256
+    A = inputs.uniform(n, n, seed=41)
+    b = inputs.vector(n, seed=42)
+    for s in (3, 5, 8):
+        dA, ipiv, _ = _factor(gpu_lib, A, 64, s)
+        db = ColMajor.from_numpy(b)
+        gpu_lib.dgetrs(dA, ipiv, db)
+        g = residual.backward_error(A, db.numpy()[:, 0], b)
+        LU, piv, _ = olu.getrf(A, nb=64, update="emulated", s=s)
+        o = residual.backward_error(A, olu.getrs(LU, piv, b), b)
+        assert o / 30 < g < o * 30, (s, g, o)
+        if s == 3:
+            assert g > 16
+        if s == 8:
+            assert g < 16
+
+
+@pytest.mark.parametrize("n", [16, 40, 60])
+def test_wilkinson_growth_exact(gpu_lib, n):
+    """Integer entries: every emulated product is exact, so the factors equal
+    the FP64 ones and max|U| = 2^(n-1) exactly (Section 5)."""
+    A = inputs.wilkinson(n)
+    dA, ipiv, info = _factor(gpu_lib, A, 16, 7)
+    assert info == 0
+    LU = dA.numpy()
+    assert (ipiv.cpu().numpy() == np.arange(1, n + 1)).all()
+    assert np.abs(np.triu(LU)).max() == 2.0 ** (n - 1)
+    LUo, _, _ = olu.getrf(A, nb=16)
+    assert np.array_equal(LU, LUo)
+
+
+def _golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                rows.append([float(Fraction(t)) for t in line.split()])
+    return np.array(rows)
+
+
+@pytest.mark.parametrize("name,A", [
+    ("eq10_turing_inverse.txt", inputs.turing(5)),
+    ("eq11_fibonacci_inverse.txt", inputs.parawilk(5, 2, 2, 0.0)),
+    ("eq13_blocked_inverse.txt", inputs.parawilk(5, 5, 2, 1.0)),
+])
+def test_worked_inverses(gpu_lib, name, A):
+    dA, ipiv, info = _factor(gpu_lib, A, 16, 7)
+    assert info == 0
+    dB = ColMajor.from_numpy(np.eye(5))
+    gpu_lib.dgetrs(dA, ipiv, dB)
+    assert np.abs(dB.numpy() - _golden(name)).max() <= 1e-15
+
+
+def test_singular_info(gpu_lib):
+    n = 200
+    A = inputs.uniform(n, n, seed=50)
+    A[:, 77] = 0.0
+    _, _, info = _factor(gpu_lib, A, 32, 7)
+    assert info == 78
+
+
+def test_multiple_rhs(gpu_lib):
+    n, nrhs = 300, 5
+    A = inputs.uniform(n, n, seed=60)
+    B = inputs.uniform(n, nrhs, seed=61)
+    dA, ipiv, _ = _factor(gpu_lib, A, 64, 8)
+    dB = ColMajor.from_numpy(B, ld=n + 3)
+    gpu_lib.dgetrs(dA, ipiv, dB)
+    X = dB.numpy()
+    for j in range(nrhs):
+        assert residual.backward_error(A, X[:, j], B[:, j]) < 16
+
+
+@pytest.mark.parametrize("n,nb,cond", [(130, 32, 1e2), (512, 64, 1e8), (1000, 128, 1e12)])
+@pytest.mark.parametrize("s", [7, 8])
+def test_potrf_potrs(gpu_lib, n, nb, cond, s):
+    A = inputs.spd(n, cond, seed=70 + n)
+    b = inputs.vector(n, seed=71)
+    dA = ColMajor.from_numpy(A)
+    info = gpu_lib.dpotrf(dA, nb=nb, slices=s)
+    gpu_lib.sync_status()
+    assert int(info.item()) == 0
+    L = np.tril(dA.numpy())
+    assert residual.chol_residual(A, L) < 16
+    # the strictly upper triangle is left untouched
+    assert np.array_equal(np.triu(dA.numpy(), 1), np.triu(A, 1))
+    db = ColMajor.from_numpy(b)
+    gpu_lib.dpotrs(dA, db)
+    x = db.numpy()[:, 0]
+    assert residual.backward_error(A, x, b) < 16
+
+
+def test_potrf_not_spd(gpu_lib):
+    A = inputs.spd(200, 10.0, seed=80)
+    A[150, 150] = -5.0
+    dA = ColMajor.from_numpy(A)
+    info = gpu_lib.dpotrf(dA, nb=32, slices=7)
+    assert int(info.item()) == 151
+
+
+@pytest.mark.parametrize("n", [4096])
+def test_getrf_large_backward_error(gpu_lib, n):
+    A = inputs.uniform(n, n, seed=90)
+    b = inputs.vector(n, seed=91)
+    dA, ipiv, info = _factor(gpu_lib, A, 128, 7)
+    assert info == 0 and _valid_ipiv(ipiv, n)
+    db = ColMajor.from_numpy(b)
+    gpu_lib.dgetrs(dA, ipiv, db)
+    x = db.numpy()[:, 0]
+    assert residual.backward_error(A, x, b) < 16
