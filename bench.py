@@ -297,7 +297,7 @@ def main():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=32768)
-    p.add_argument("--nb", type=int, default=128)
+    p.add_argument("--nb", type=int, default=256)
     p.add_argument("--slices", type=int, default=7)
     p.add_argument("--cpu-n", type=int, default=512)
     p.add_argument("--e2e-steps", type=int, default=1)

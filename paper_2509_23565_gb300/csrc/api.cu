@@ -38,58 +38,87 @@ int pairs_at(int s, int L) {
   return n;
 }
 
-// Build the sweep schedule: levels in ascending order; a level whose pairs fit
-// the exactness budget over the whole K is one job, otherwise it is split into
-// K segments; consecutive single-job levels are paired into one sweep.  In the
-// narrow variant the last level is a separate held sweep.  Returns false if
-// the narrow variant cannot hold the last level in one job.
+// Build the sweep schedule.  Jobs: a level L whose n_L slice pairs fit the
+// exactness budget over the whole K (n_L * K <= 1040) is one job; otherwise
+// (narrow variant) its pairs are split into groups that fit, or (wide variant)
+// its K range is split into segments.  Levels are consumed in ascending order;
+// consecutive jobs of one K range are paired into sweeps.  In the narrow
+// variant the last level's jobs (at most two) form a final held sweep.
 bool build_schedule(int s, int nch, bool wide, std::vector<Sweep>& out) {
   out.clear();
   const int t = s + 1;
-  auto cmax = [&](int L) {
-    const int n = pairs_at(s, L);
-    int c = kExactBudget / (kBK * n);
-    return c < 1 ? 1 : c;
+  struct Job {
+    int L, pb, pe, c0, c1;
   };
-  auto planes = [&](int L) { return L - 1 < s ? L - 1 : s; };
-  int L = 2;
-  while (L <= t) {
-    if (!wide && L == t) {
-      if (nch > cmax(L)) return false;
-      out.push_back(Sweep{0, static_cast<int16_t>(nch), static_cast<int8_t>(L), 0, 1, static_cast<int8_t>(planes(L))});
-      break;
+  std::vector<Job> jobs, held;
+  const int kc = nch * kBK;
+  for (int L = 2; L <= t; ++L) {
+    const int pb = L - s > 1 ? L - s : 1;
+    const int pe = L - 1 < s ? L - 1 : s;
+    const int n = pe - pb + 1;
+    std::vector<Job>& dst = (!wide && L == t) ? held : jobs;
+    if (n * kc <= kExactBudget) {
+      dst.push_back(Job{L, pb, pe, 0, nch});
+    } else if (!wide) {
+      const int per = kExactBudget / kc;          // pairs per job
+      if (per < 1) return false;
+      for (int p = pb; p <= pe; p += per) dst.push_back(Job{L, p, p + per - 1 < pe ? p + per - 1 : pe, 0, nch});
+    } else {
+      int cm = kExactBudget / (kBK * n);
+      if (cm < 1) cm = 1;
+      for (int c0 = 0; c0 < nch; c0 += cm) dst.push_back(Job{L, pb, pe, c0, c0 + cm < nch ? c0 + cm : nch});
     }
-    if (nch <= cmax(L)) {
-      const bool next_ok = (L + 1 <= t) && (wide || L + 1 < t) && nch <= cmax(L + 1);
-      if (next_ok) {
-        out.push_back(Sweep{0, static_cast<int16_t>(nch), static_cast<int8_t>(L), static_cast<int8_t>(L + 1), 0,
-                            static_cast<int8_t>(planes(L + 1))});
-        L += 2;
-        continue;
-      }
-      out.push_back(Sweep{0, static_cast<int16_t>(nch), static_cast<int8_t>(L), 0, 0, static_cast<int8_t>(planes(L))});
-      L += 1;
-      continue;
+  }
+  if (held.size() > 2) return false;
+  auto planes_of = [&](const Job& j) { return j.pe > j.L - j.pb ? j.pe : j.L - j.pb; };
+  for (size_t i = 0; i < jobs.size();) {
+    Sweep sw{};
+    sw.k0c = static_cast<int16_t>(jobs[i].c0);
+    sw.k1c = static_cast<int16_t>(jobs[i].c1);
+    sw.L[0] = static_cast<int8_t>(jobs[i].L);
+    sw.pb[0] = static_cast<int8_t>(jobs[i].pb);
+    sw.pe[0] = static_cast<int8_t>(jobs[i].pe);
+    int np = planes_of(jobs[i]);
+    size_t used = 1;
+    if (i + 1 < jobs.size() && jobs[i + 1].c0 == jobs[i].c0 && jobs[i + 1].c1 == jobs[i].c1) {
+      sw.L[1] = static_cast<int8_t>(jobs[i + 1].L);
+      sw.pb[1] = static_cast<int8_t>(jobs[i + 1].pb);
+      sw.pe[1] = static_cast<int8_t>(jobs[i + 1].pe);
+      np = np > planes_of(jobs[i + 1]) ? np : planes_of(jobs[i + 1]);
+      used = 2;
     }
-    for (int c0 = 0; c0 < nch; c0 += cmax(L)) {
-      const int c1 = c0 + cmax(L) < nch ? c0 + cmax(L) : nch;
-      out.push_back(Sweep{static_cast<int16_t>(c0), static_cast<int16_t>(c1), static_cast<int8_t>(L), 0, 0,
-                          static_cast<int8_t>(planes(L))});
+    sw.nplanes = static_cast<int8_t>(np);
+    out.push_back(sw);
+    i += used;
+  }
+  if (!held.empty()) {
+    Sweep sw{};
+    sw.k0c = 0;
+    sw.k1c = static_cast<int16_t>(nch);
+    sw.held = 1;
+    int np = 0;
+    for (size_t j = 0; j < held.size(); ++j) {
+      sw.L[j] = static_cast<int8_t>(held[j].L);
+      sw.pb[j] = static_cast<int8_t>(held[j].pb);
+      sw.pe[j] = static_cast<int8_t>(held[j].pe);
+      np = np > planes_of(held[j]) ? np : planes_of(held[j]);
     }
-    L += 1;
+    sw.nplanes = static_cast<int8_t>(np);
+    out.push_back(sw);
   }
   return true;
 }
 
 // The narrow variant keeps the Horner state in int64 and rounds T = R 2^7 + I
-// with a 64-bit magnitude: it needs |R| < 2^57 and the last level in one job.
+// on a 64-bit magnitude (a 128-bit path covers |R| >= 2^57): it needs the last
+// level in at most two jobs and |R| well inside int64.
 bool narrow_ok(int s, int k) {
   if (s > 7) return false;
   const int nch = (k + kBK - 1) / kBK;
   std::vector<Sweep> tmp;
   if (!build_schedule(s, nch, false, tmp)) return false;
   const long double bound = horner_bound_per_k(s) * static_cast<long double>(nch * kBK);
-  return bound < 1.44e17L;   // 2^57
+  return bound < 4.0e18L;   // < 2^62
 }
 
 int get_schedule(emul_handle_t h, int s, int nch, bool wide, Sweep** dptr, int* count) {

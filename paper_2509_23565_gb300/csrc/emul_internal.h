@@ -11,12 +11,14 @@ constexpr int kMaxSlices = 8;
 constexpr int kBK = 32;                  // K elements per staged chunk (64 B of BF16: SWIZZLE_64B)
 constexpr int kExactBudget = 1040;       // k * pairs per accumulator: 1040 * 127^2 < 2^24
 
-// One sweep of the product schedule: the MMAs of one or two levels over the
-// K chunks [k0c, k1c), sharing the staged slice tiles of each chunk.
+// One sweep of the product schedule: one or two accumulator jobs over the K
+// chunks [k0c, k1c), sharing the staged slice tiles of each chunk.  A job
+// sums the slice pairs (p, L-p), p = pb..pe, of one level L into one TMEM slot.
 struct Sweep {
   int16_t k0c, k1c;   // chunk range
-  int8_t L0, L1;      // levels (L1 = 0: single level)
-  int8_t last;        // 1: L0 is the last level and is held for the final step
+  int8_t L[2];        // job levels (L[1] = 0: one job)
+  int8_t pb[2], pe[2];// pair ranges
+  int8_t held;        // 1: the jobs are the last level, held for the final step
   int8_t nplanes;     // slice planes 1..nplanes of A and of B are staged
 };
 

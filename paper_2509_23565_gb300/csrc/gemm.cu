@@ -53,7 +53,7 @@ struct Cfg {
 // Correctly rounded double of T * 2^sh (round to nearest even), computed with
 // integer operations on the IEEE-754 fields (overflow gives +-inf, results
 // below the normal range are rounded as subnormals).
-__device__ __forceinline__ double rn_scaled(__int128 T, int sh) {
+__device__ __noinline__ double rn_scaled(__int128 T, int sh) {
   if (T == 0) return 0.0;
   const bool neg = T < 0;
   const unsigned __int128 mag = neg ? (unsigned __int128)(-(T + 1)) + 1u : (unsigned __int128)T;
@@ -77,12 +77,13 @@ __device__ __forceinline__ double rn_scaled(__int128 T, int sh) {
   return __longlong_as_double((long long)(sign | bits));
 }
 
-// Fast path of rn_scaled for T = R * 2^7 + I with |R| < 2^57 and |I| < 2^24
+// Fast path of rn_scaled for T = R * 2^7 + I with |R| < 2^56 and |I| < 2^26
 // (the narrow variant), where |T| < 2^64 fits an unsigned 64-bit magnitude.
 // Results outside the normal exponent range take the generic path.
 __device__ __forceinline__ double rn_scaled_r7(long long R, int I, int sh) {
   const bool rneg = R < 0;
   const unsigned long long aR = rneg ? 0ull - (unsigned long long)R : (unsigned long long)R;
+  if (aR >> 56) return rn_scaled((__int128)R * 128 + (__int128)I, sh);   // |T| may exceed 2^63
   const long long Is = rneg ? -(long long)I : (long long)I;
   unsigned long long u = (aR << 7) + (unsigned long long)Is;
   bool neg = rneg;
@@ -234,8 +235,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
         for (int sw = 0; sw < a.nsweeps && ok; ++sw) {
           const Sweep S = a.sched[sw];
-          const int nj = S.L1 ? 2 : 1;
-          const int lev[2] = {S.L0, S.L1};
+          const int nj = S.L[1] ? 2 : 1;
           uint32_t dcol[2];
           for (int j = 0; j < nj; ++j) {
             const long u = jc + j;
@@ -259,9 +259,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const uint32_t base = smem_u32(smem + (size_t)st * stage_bytes);
             for (int j = 0; j < nj; ++j) {
-              const int L = lev[j];
-              const int pb = L - s > 1 ? L - s : 1;
-              const int pe = L - 1 < s ? L - 1 : s;
+              const int L = S.L[j];
+              const int pb = S.pb[j];
+              const int pe = S.pe[j];
               for (int p = pb; p <= pe; ++p) {
                 const int q = L - p;
                 const uint32_t aa = base + (uint32_t)(p - 1) * Cf::A_TILE;
@@ -324,9 +324,63 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool held_final = false;
       for (int sw = 0; sw < a.nsweeps && ok; ++sw) {
         const Sweep S = a.sched[sw];
-        const int nj = S.L1 ? 2 : 1;
+        const int nj = S.L[1] ? 2 : 1;
+        if (S.held && a.mode == 0) {
+          // final step: T = R * 2^7 + (sum of the held jobs of the last level),
+          // rounded once, C updated in place
+          held_final = true;
+          int slots[2];
+          for (int j = 0; j < nj && ok; ++j) {
+            slots[j] = (int)((jc + j) % kSlots);
+            if (aborted(abortp) ||
+                !mbar_wait(&slot_full[slots[j]], (uint32_t)(((jc + j) / kSlots) & 1), a.wait_limit)) {
+              if (!aborted(abortp)) raise_timeout(a, abortp);
+              ok = false;
+            }
+          }
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t ta0 = tmem + lane_addr + (uint32_t)(slots[0] * Cf::BN + half * CPT);
+          const uint32_t ta1 = tmem + lane_addr + (uint32_t)(slots[nj - 1] * Cf::BN + half * CPT);
+          const bool rowok = row < a.M;
+#pragma unroll
+          for (int c8 = 0; c8 < CPT / 8; ++c8) {
+            uint32_t r0[8], r1[8];
+            tmem_ld8(ta0 + c8 * 8, r0);
+            tmem_ld8(ta1 + c8 * 8, r1);
+            double cv[8];
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+              const int col = col0 + c8 * 8 + jj;
+              cv[jj] = (needs_c && rowok && col < a.N) ? a.C[row + (long)col * a.ldc] : 0.0;
+            }
+            tmem_ld_wait();
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+              const int c = c8 * 8 + jj;
+              const int col = col0 + c;
+              const int f = __shfl_sync(0xFFFFFFFFu, fcol[c / 32], c % 32);
+              if (!rowok || col >= a.N || (a.lower && row < col)) continue;
+              const int I = f2i(r0[jj]) + (nj == 2 ? f2i(r1[jj]) : 0);
+              double D;
+              if (e_row == kNonFinite || f == kNonFinite)
+                D = __longlong_as_double(0x7FF8000000000000ll);
+              else if (WIDE)
+                D = rn_scaled((__int128)R[c] * 128 + (__int128)I, e_row + f + sh0);
+              else
+                D = rn_scaled_r7((long long)R[c], I, e_row + f + sh0);
+              a.C[row + (long)col * a.ldc] = apply_update<UPD>(a, D, cv[jj]);
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0)
+            for (int j = 0; j < nj; ++j) mbar_arrive(&slot_empty[slots[j]]);
+          jc += nj;
+          continue;
+        }
         for (int j = 0; j < nj; ++j) {
-          const int L = j ? S.L1 : S.L0;
+          const int L = S.L[j];
           const int slot = (int)(jc % kSlots);
           if (aborted(abortp) || !mbar_wait(&slot_full[slot], (uint32_t)((jc / kSlots) & 1), a.wait_limit)) {
             if (!aborted(abortp)) raise_timeout(a, abortp);
@@ -336,7 +390,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_after();
           const uint32_t taddr = tmem + lane_addr + (uint32_t)(slot * Cf::BN + half * CPT);
           if (a.mode == 1) {
-            // level sums out (exact int32), added so that K segments accumulate
+            // level sums out (exact int32), added so that K segments / pair groups accumulate
 #pragma unroll
             for (int c16 = 0; c16 < CPT / 16; ++c16) {
               uint32_t r[16];
@@ -349,37 +403,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                   int32_t* lp = a.levels + (long)(L - 2) * a.ldl_plane + row + (long)col * a.ldl;
                   *lp += f2i(r[jj]);
                 }
-              }
-            }
-          } else if (S.last) {
-            // final step: T = R * 2^7 + I_t, rounded once, C updated in place
-            held_final = true;
-#pragma unroll
-            for (int c8 = 0; c8 < CPT / 8; ++c8) {
-              uint32_t r[8];
-              tmem_ld8(taddr + c8 * 8, r);
-              double cv[8];
-              const bool rowok = row < a.M;
-#pragma unroll
-              for (int jj = 0; jj < 8; ++jj) {
-                const int col = col0 + c8 * 8 + jj;
-                cv[jj] = (needs_c && rowok && col < a.N) ? a.C[row + (long)col * a.ldc] : 0.0;
-              }
-              tmem_ld_wait();
-#pragma unroll
-              for (int jj = 0; jj < 8; ++jj) {
-                const int c = c8 * 8 + jj;
-                const int col = col0 + c;
-                const int f = __shfl_sync(0xFFFFFFFFu, fcol[c / 32], c % 32);
-                if (!rowok || col >= a.N || (a.lower && row < col)) continue;
-                double D;
-                if (e_row == kNonFinite || f == kNonFinite)
-                  D = __longlong_as_double(0x7FF8000000000000ll);
-                else if (WIDE)
-                  D = rn_scaled((__int128)R[c] * 128 + (__int128)f2i(r[jj]), e_row + f + sh0);
-                else
-                  D = rn_scaled_r7((long long)R[c], f2i(r[jj]), e_row + f + sh0);
-                a.C[row + (long)col * a.ldc] = apply_update<UPD>(a, D, cv[jj]);
               }
             }
           } else {

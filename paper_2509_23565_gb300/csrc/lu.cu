@@ -199,18 +199,87 @@ __global__ void __launch_bounds__(kLeafThreads) getf2_leaf_kernel(double* A, lon
     for (int lr = tid; lr < rcount; lr += blockDim.x) A[(d0 + r0 + lr) + static_cast<long>(d0 + c) * lda] = P[c * R + lr];
 }
 
-// Row interchanges ipiv[k1..k2) (1-based global rows) applied to columns [c0, c1).
-__global__ void laswp_kernel(double* A, long lda, int c0, int c1, const int32_t* ipiv, int k1, int k2) {
-  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= c1) return;
-  double* col = A + static_cast<long>(c) * lda;
+// Row interchanges ipiv[k1..k2) (1-based global rows, ipiv[k]-1 >= k) resolved
+// into a gather map: after the interchanges, row dst[i] holds the original row
+// src[i], for the *count affected rows (at most 2 (k2-k1)).  Rows k < k2 are
+// final once interchange k is done, so one pass with a small hash of the rows
+// beyond the block suffices.  One thread.
+constexpr int kPermMax = 256;          // interchanges per block (nb <= 256)
+constexpr int kHash = 1024;
+__global__ void laswp_perm_kernel(const int32_t* ipiv, int k1, int k2, int* map /* [2][2*kPermMax] + count */) {
+  __shared__ int cont[kPermMax];                 // content of rows k1..k2-1
+  __shared__ int hkey[kHash], hval[kHash];       // rows >= k2 that were touched
+  __shared__ int order[kPermMax];
+  if (threadIdx.x != 0) return;
+  const int nb = k2 - k1;
+  for (int i = 0; i < nb; ++i) cont[i] = k1 + i;
+  for (int i = 0; i < kHash; ++i) hkey[i] = -1;
+  int nout = 0;
+  auto slot_of = [&](int row) {
+    int h = (row * 2654435761u) & (kHash - 1);
+    while (hkey[h] != -1 && hkey[h] != row) h = (h + 1) & (kHash - 1);
+    return h;
+  };
   for (int k = k1; k < k2; ++k) {
     const int p = ipiv[k] - 1;
-    if (p != k) {
-      const double t = col[k];
-      col[k] = col[p];
-      col[p] = t;
+    if (p == k) continue;
+    if (p < k2) {
+      const int t = cont[k - k1];
+      cont[k - k1] = cont[p - k1];
+      cont[p - k1] = t;
+    } else {
+      const int h = slot_of(p);
+      if (hkey[h] == -1) {
+        hkey[h] = p;
+        hval[h] = p;
+        order[nout++] = h;
+      }
+      const int t = cont[k - k1];
+      cont[k - k1] = hval[h];
+      hval[h] = t;
     }
+  }
+  int* dst = map;
+  int* src = map + 2 * kPermMax;
+  int cnt = 0;
+  for (int i = 0; i < nb; ++i)
+    if (cont[i] != k1 + i) {
+      dst[cnt] = k1 + i;
+      src[cnt] = cont[i];
+      ++cnt;
+    }
+  for (int j = 0; j < nout; ++j) {
+    const int h = order[j];
+    if (hval[h] != hkey[h]) {
+      dst[cnt] = hkey[h];
+      src[cnt] = hval[h];
+      ++cnt;
+    }
+  }
+  map[4 * kPermMax] = cnt;
+}
+
+// Apply the gather map to columns [c0, c1): each block owns 8 columns, reads
+// every source row into shared memory, then writes the destinations.
+constexpr int kSwpCols = 8;
+__global__ void __launch_bounds__(256) laswp_apply_kernel(double* A, long lda, int c0, int c1, const int* map) {
+  __shared__ double buf[2 * kPermMax][kSwpCols];
+  __shared__ int dst_s[2 * kPermMax], src_s[2 * kPermMax];
+  const int cnt = map[4 * kPermMax];
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    dst_s[i] = map[i];
+    src_s[i] = map[2 * kPermMax + i];
+  }
+  __syncthreads();
+  const int cb = c0 + blockIdx.x * kSwpCols;
+  for (int e = threadIdx.x; e < cnt * kSwpCols; e += blockDim.x) {
+    const int i = e % cnt, j = e / cnt;
+    if (cb + j < c1) buf[i][j] = A[src_s[i] + static_cast<long>(cb + j) * lda];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < cnt * kSwpCols; e += blockDim.x) {
+    const int i = e % cnt, j = e / cnt;
+    if (cb + j < c1) A[dst_s[i] + static_cast<long>(cb + j) * lda] = buf[i][j];
   }
 }
 
@@ -288,14 +357,15 @@ __global__ void potf2_kernel(double* A, long lda, int d0, int nb, int32_t* info)
 // where T is stored lower).  One block per right-hand side.
 __global__ void trsv_block_kernel(const double* T, long ldt, double* X, long ldx, int d0, int bs, int lower, int unit,
                                   int trans) {
+  extern __shared__ double tb[];   // the bs x bs diagonal block, tb[r + c*bs] = T(d0+r, d0+c) as stored
   __shared__ double x[128];
   double* xc = X + static_cast<long>(blockIdx.x) * ldx + d0;
   const int i = threadIdx.x;
+  for (int c = 0; c < bs; ++c)
+    if (i < bs) tb[i + c * bs] = T[(d0 + i) + static_cast<long>(d0 + c) * ldt];
   if (i < bs) x[i] = xc[i];
   __syncthreads();
-  auto t = [&](int r, int c) -> double {
-    return trans ? T[(d0 + c) + static_cast<long>(d0 + r) * ldt] : T[(d0 + r) + static_cast<long>(d0 + c) * ldt];
-  };
+  auto t = [&](int r, int c) -> double { return trans ? tb[c + r * bs] : tb[r + c * bs]; };
   if (lower) {
     for (int k = 0; k < bs; ++k) {
       if (!unit && i == k) x[k] = x[k] / t(k, k);
@@ -388,11 +458,14 @@ struct LuBufs {
   double* diag_rows;    // [2][kLeaf]
   GridBar* bar;
   unsigned long long* racc;
+  int* map;             // laswp gather maps, [4*kPermMax + 1] ints each, one per recursion depth
 };
+constexpr int kMapInts = 4 * kPermMax + 8;
+constexpr int kMaxDepth = 8;
 
 size_t lu_extra_bytes(int nb, int nsm) {
   return al(static_cast<size_t>(nb) * nb * 8) + al(2ull * nsm * kLeaf * 8) + al(2ull * nsm * 8) + al(2ull * nsm * 4) +
-         al(2ull * kLeaf * 8) + al(sizeof(GridBar)) + al(4 * 8) + kAl;
+         al(2ull * kLeaf * 8) + al(sizeof(GridBar)) + al(4 * 8) + al(kMaxDepth * kMapInts * 4) + kAl;
 }
 
 LuBufs carve(emul_handle_t h, size_t off, int nb) {
@@ -411,13 +484,15 @@ LuBufs carve(emul_handle_t h, size_t off, int nb) {
   b.bar = reinterpret_cast<GridBar*>(p);
   p += al(sizeof(GridBar));
   b.racc = reinterpret_cast<unsigned long long*>(p);
+  p += al(4 * 8);
+  b.map = reinterpret_cast<int*>(p);
   return b;
 }
 
 int launch_leaf(emul_handle_t h, double* A, long lda, int n, int d0, int w, int32_t* ipiv, int32_t* info,
                 const LuBufs& B) {
   const int mp = n - d0;
-  int G = (mp + 511) / 512;
+  int G = (mp + 255) / 256;
   const int smem_rows_cap = 200 * 1024 / (w * 8);
   if ((mp + G - 1) / G > smem_rows_cap) G = (mp + smem_rows_cap - 1) / smem_rows_cap;
   if (G < 1) G = 1;
@@ -444,22 +519,40 @@ int launch_leaf(emul_handle_t h, double* A, long lda, int n, int d0, int w, int3
                     "panel leaf");
 }
 
-int laswp(emul_handle_t h, double* A, long lda, int c0, int c1, const int32_t* ipiv, int k1, int k2) {
-  if (c1 <= c0 || k2 <= k1) return EMUL_OK;
-  laswp_kernel<<<(c1 - c0 + 127) / 128, 128, 0, h->stream>>>(A, lda, c0, c1, ipiv, k1, k2);
+// Resolve the interchanges ipiv[k1..k2) into the gather map (once per block).
+int laswp_prepare(emul_handle_t h, const int32_t* ipiv, int k1, int k2, int* map) {
+  if (k2 <= k1) return EMUL_OK;
+  if (k2 - k1 > kPermMax) return set_error(h, EMUL_INVALID_ARG, "too many interchanges in one block");
+  laswp_perm_kernel<<<1, 32, 0, h->stream>>>(ipiv, k1, k2, map);
+  h->launches++;
+  return check_cuda(h, cudaGetLastError(), "laswp map");
+}
+
+// Apply a prepared gather map to columns [c0, c1).
+int laswp_apply(emul_handle_t h, double* A, long lda, int c0, int c1, const int* map) {
+  if (c1 <= c0) return EMUL_OK;
+  laswp_apply_kernel<<<(c1 - c0 + kSwpCols - 1) / kSwpCols, 256, 0, h->stream>>>(A, lda, c0, c1, map);
   h->launches++;
   return check_cuda(h, cudaGetLastError(), "laswp");
 }
 
+int laswp(emul_handle_t h, double* A, long lda, int c0, int c1, const int32_t* ipiv, int k1, int k2, int* map) {
+  if (c1 <= c0 || k2 <= k1) return EMUL_OK;
+  int rc = laswp_prepare(h, ipiv, k1, k2, map);
+  if (rc) return rc;
+  return laswp_apply(h, A, lda, c0, c1, map);
+}
+
 // Recursive panel factorization of rows d0..n-1, columns d0..d0+w-1.
 int rgetrf(emul_handle_t h, double* A, long lda, int n, int d0, int w, int32_t* ipiv, int32_t* info, int s,
-           const LuBufs& B) {
+           const LuBufs& B, int depth = 1) {
   if (w <= kLeaf) return launch_leaf(h, A, lda, n, d0, w, ipiv, info, B);
+  int* map = B.map + depth * kMapInts;
   const int w1 = (w / 2 + 7) / 8 * 8;
   const int w2 = w - w1;
-  int rc = rgetrf(h, A, lda, n, d0, w1, ipiv, info, s, B);
+  int rc = rgetrf(h, A, lda, n, d0, w1, ipiv, info, s, B, depth + 1);
   if (rc) return rc;
-  rc = laswp(h, A, lda, d0 + w1, d0 + w, ipiv, d0, d0 + w1);
+  rc = laswp(h, A, lda, d0 + w1, d0 + w, ipiv, d0, d0 + w1, map);
   if (rc) return rc;
   trsm_small_kernel<<<w2, 128, 0, h->stream>>>(A, lda, d0, w1, d0 + w1);
   h->launches++;
@@ -471,12 +564,20 @@ int rgetrf(emul_handle_t h, double* A, long lda, int n, int d0, int w, int32_t* 
                 Operand{A + d0 + static_cast<long>(d0 + w1) * lda, lda, 1}, 1.0,
                 A + (d0 + w1) + static_cast<long>(d0 + w1) * lda, lda, s, false, 0, nullptr, 0, 0);
   if (rc) return rc;
-  rc = rgetrf(h, A, lda, n, d0 + w1, w2, ipiv, info, s, B);
+  rc = rgetrf(h, A, lda, n, d0 + w1, w2, ipiv, info, s, B, depth + 1);
   if (rc) return rc;
-  return laswp(h, A, lda, d0, d0 + w1, ipiv, d0 + w1, d0 + w);
+  return laswp(h, A, lda, d0, d0 + w1, ipiv, d0 + w1, d0 + w, map);
 }
 
 }  // namespace
+
+void trsv_attr() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(trsv_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 8);
+    done = true;
+  }
+}
 
 }  // namespace emul
 
@@ -503,9 +604,11 @@ int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int n
     const int jb = nb < n - j0 ? nb : n - j0;
     rc = emul::rgetrf(h, A, lda, n, j0, jb, ipiv, info, slices, B);
     if (rc) return rc;
-    rc = emul::laswp(h, A, lda, 0, j0, ipiv, j0, j0 + jb);
+    rc = emul::laswp_prepare(h, ipiv, j0, j0 + jb, B.map);
     if (rc) return rc;
-    rc = emul::laswp(h, A, lda, j0 + jb, n, ipiv, j0, j0 + jb);
+    rc = emul::laswp_apply(h, A, lda, 0, j0, B.map);
+    if (rc) return rc;
+    rc = emul::laswp_apply(h, A, lda, j0 + jb, n, B.map);
     if (rc) return rc;
     const int m2 = n - j0 - jb;
     if (m2 > 0) {
@@ -531,16 +634,23 @@ int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int n
 
 int emul_dgetrs(emul_handle_t h, int n, int nrhs, const double* LU, int lda, const int32_t* ipiv, double* B,
                 int ldb) {
+  emul::trsv_attr();
   if (!h) return EMUL_INVALID_ARG;
   if (n < 0 || nrhs < 0 || lda < (n > 1 ? n : 1) || ldb < (n > 1 ? n : 1) || (n > 0 && nrhs > 0 && (!LU || !ipiv || !B)))
     return emul::set_error(h, EMUL_INVALID_ARG, "emul_dgetrs: invalid argument");
   if (n == 0 || nrhs == 0) return EMUL_OK;
-  int rc = emul::laswp(h, B, ldb, 0, nrhs, ipiv, 0, n);
+  const size_t need = emul::lu_extra_bytes(16, h->nsm);
+  int rc = emul::reserve_workspace(h, need);
   if (rc) return rc;
+  const emul::LuBufs W = emul::carve(h, 0, 16);
+  for (int k = 0; k < n; k += emul::kPermMax) {
+    rc = emul::laswp(h, B, ldb, 0, nrhs, ipiv, k, k + emul::kPermMax < n ? k + emul::kPermMax : n, W.map);
+    if (rc) return rc;
+  }
   constexpr int bs = 128;  // diagonal blocks of the substitution
   for (int d0 = 0; d0 < n; d0 += bs) {
     const int b = bs < n - d0 ? bs : n - d0;
-    emul::trsv_block_kernel<<<nrhs, 128, 0, h->stream>>>(LU, lda, B, ldb, d0, b, 1, 1, 0);
+    emul::trsv_block_kernel<<<nrhs, 128, b * b * sizeof(double), h->stream>>>(LU, lda, B, ldb, d0, b, 1, 1, 0);
     h->launches += (d0 + b < n) ? 2 : 1;
     if (d0 + b < n)
       emul::gemv_update_kernel<<<dim3((n - d0 - b + 255) / 256, nrhs), 256, 0, h->stream>>>(LU, lda, B, ldb, d0 + b,
@@ -548,7 +658,7 @@ int emul_dgetrs(emul_handle_t h, int n, int nrhs, const double* LU, int lda, con
   }
   for (int d0 = ((n - 1) / bs) * bs; d0 >= 0; d0 -= bs) {
     const int b = bs < n - d0 ? bs : n - d0;
-    emul::trsv_block_kernel<<<nrhs, 128, 0, h->stream>>>(LU, lda, B, ldb, d0, b, 0, 0, 0);
+    emul::trsv_block_kernel<<<nrhs, 128, b * b * sizeof(double), h->stream>>>(LU, lda, B, ldb, d0, b, 0, 0, 0);
     h->launches += (d0 > 0) ? 2 : 1;
     if (d0 > 0)
       emul::gemv_update_kernel<<<dim3((d0 + 255) / 256, nrhs), 256, 0, h->stream>>>(LU, lda, B, ldb, 0, d0, d0, b, 0);
@@ -599,6 +709,7 @@ int emul_dpotrf(emul_handle_t h, char uplo, int n, double* A, int lda, int nb, i
 }
 
 int emul_dpotrs(emul_handle_t h, char uplo, int n, int nrhs, const double* L, int lda, double* B, int ldb) {
+  emul::trsv_attr();
   if (!h) return EMUL_INVALID_ARG;
   if ((uplo != 'L' && uplo != 'l') || n < 0 || nrhs < 0 || lda < (n > 1 ? n : 1) || ldb < (n > 1 ? n : 1) ||
       (n > 0 && nrhs > 0 && (!L || !B)))
@@ -607,7 +718,7 @@ int emul_dpotrs(emul_handle_t h, char uplo, int n, int nrhs, const double* L, in
   constexpr int bs = 128;
   for (int d0 = 0; d0 < n; d0 += bs) {
     const int b = bs < n - d0 ? bs : n - d0;
-    emul::trsv_block_kernel<<<nrhs, 128, 0, h->stream>>>(L, lda, B, ldb, d0, b, 1, 0, 0);
+    emul::trsv_block_kernel<<<nrhs, 128, b * b * sizeof(double), h->stream>>>(L, lda, B, ldb, d0, b, 1, 0, 0);
     h->launches += (d0 + b < n) ? 2 : 1;
     if (d0 + b < n)
       emul::gemv_update_kernel<<<dim3((n - d0 - b + 255) / 256, nrhs), 256, 0, h->stream>>>(L, lda, B, ldb, d0 + b,
@@ -615,7 +726,7 @@ int emul_dpotrs(emul_handle_t h, char uplo, int n, int nrhs, const double* L, in
   }
   for (int d0 = ((n - 1) / bs) * bs; d0 >= 0; d0 -= bs) {
     const int b = bs < n - d0 ? bs : n - d0;
-    emul::trsv_block_kernel<<<nrhs, 128, 0, h->stream>>>(L, lda, B, ldb, d0, b, 0, 0, 1);
+    emul::trsv_block_kernel<<<nrhs, 128, b * b * sizeof(double), h->stream>>>(L, lda, B, ldb, d0, b, 0, 0, 1);
     h->launches += (d0 > 0) ? 2 : 1;
     if (d0 > 0)
       emul::gemv_update_kernel<<<dim3((d0 + 7) / 8, nrhs), 256, 0, h->stream>>>(L, lda, B, ldb, 0, d0, d0, b, 1);

@@ -77,7 +77,7 @@ def test_level_sums_bitexact(gpu_lib, m, n, k, s):
     gpu_lib.sync_status()
 
 
-@pytest.mark.parametrize("s,k", [(7, 128), (7, 1000), (8, 128), (8, 1040), (3, 2048)])
+@pytest.mark.parametrize("s,k", [(7, 128), (7, 256), (6, 224), (7, 1000), (8, 128), (8, 1040), (3, 2048)])
 def test_level_sums_worst_case_magnitudes(gpu_lib, s, k):
     """Every digit 127 with one sign: each accumulator reaches its largest
     allowed magnitude (k * pairs * 127^2 up to 1040 * 127^2 < 2^24)."""
@@ -94,7 +94,7 @@ def test_level_sums_worst_case_magnitudes(gpu_lib, s, k):
 
 
 @pytest.mark.parametrize("m,n,k", [(1, 1, 1), (33, 17, 5), (128, 128, 128), (257, 129, 96), (200, 380, 300),
-                                   (130, 70, 1500)])
+                                   (130, 70, 1500), (256, 200, 256), (130, 140, 192), (64, 300, 160)])
 @pytest.mark.parametrize("s", [3, 6, 7, 8])
 @pytest.mark.parametrize("alpha,beta", [(1.0, 0.0), (-1.0, 1.0), (0.5, -2.0)])
 def test_dgemm_bitexact(gpu_lib, m, n, k, s, alpha, beta):

@@ -34,7 +34,7 @@ def _valid_ipiv(ipiv, n):
     return p.shape == (n,) and (p >= np.arange(1, n + 1)).all() and (p <= n).all()
 
 
-@pytest.mark.parametrize("n,nb", [(1, 64), (5, 16), (100, 32), (257, 64), (700, 128), (1024, 64)])
+@pytest.mark.parametrize("n,nb", [(1, 64), (5, 16), (100, 32), (257, 64), (700, 128), (1024, 64), (1100, 256)])
 @pytest.mark.parametrize("s", [7, 8])
 def test_getrf_getrs_uniform(gpu_lib, n, nb, s):
     A = inputs.uniform(n, n, seed=10 + n)
