@@ -30,12 +30,12 @@ namespace emul {
 
 namespace {
 
-constexpr int kThreads = 384;          // 3 warpgroups: producer/MMA, 2 x epilogue
-constexpr int kLaunchRegs = 168;        // 384 x 168 = 64512 registers at launch
-constexpr int kLowRegs = 40;            // producer warpgroup after setmaxnreg.dec
-constexpr int kHighRegs = 232;          // epilogue warpgroups: 128*40 + 256*232 = 64512
+constexpr int kThreads = 640;          // 5 warpgroups: producer/MMA, 4 x epilogue
+constexpr int kLaunchRegs = 96;         // 640 x 96 = 61440 registers at launch
+constexpr int kLowRegs = 64;            // producer warpgroup after setmaxnreg.dec
+constexpr int kHighRegs = 104;          // epilogue warpgroups: 128*64 + 512*104 = 61440
 constexpr int kSlots = 4;
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;
 constexpr int kMaxStages = 4;
 constexpr int kStatusTimeout = -4;
 
@@ -43,7 +43,7 @@ template <bool WIDE>
 struct Cfg {
   static constexpr int BM = 128;
   static constexpr int BN = WIDE ? 64 : 128;
-  static constexpr int CPT = BN / 2;                  // columns per epilogue thread
+  static constexpr int CPT = BN / 4;                  // columns per epilogue thread
   static constexpr uint32_t A_TILE = BM * kBK * 2;    // bytes
   static constexpr uint32_t B_TILE = BN * kBK * 2;
   static constexpr uint32_t TMEM_COLS = kSlots * BN;
@@ -289,8 +289,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kHighRegs));
     // ------------------------------------------------------------ epilogue
     const int ew = warp - 4;
-    const int quarter = warp & 3;
-    const int half = ew >> 2;
+    const int quarter = warp & 3;      // TMEM lane quarter this warp may access
+    const int half = ew >> 2;          // column group of CPT columns
     const int row_t = quarter * 32 + lane;
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
     constexpr int CPT = Cf::CPT;
@@ -306,11 +306,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int col0 = tn * Cf::BN + half * CPT;
       const int e_row = row < a.M ? a.ea[row] : 0;
       // column scales of this thread's CPT columns, one per lane (broadcast by shuffle)
-      int fcol[CPT / 32];
-#pragma unroll
-      for (int g = 0; g < CPT / 32; ++g) {
-        const int col = col0 + g * 32 + lane;
-        fcol[g] = col < a.N ? a.fb[col] : 0;
+      int fcol[1];
+      {
+        const int col = col0 + lane;
+        fcol[0] = (lane < CPT && col < a.N) ? a.fb[col] : 0;
       }
       // pull this thread's C entries into L2 while the products run
       if (needs_c && a.mode == 0 && row < a.M) {
@@ -344,22 +343,22 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t ta1 = tmem + lane_addr + (uint32_t)(slots[nj - 1] * Cf::BN + half * CPT);
           const bool rowok = row < a.M;
 #pragma unroll
-          for (int c8 = 0; c8 < CPT / 8; ++c8) {
-            uint32_t r0[8], r1[8];
-            tmem_ld8(ta0 + c8 * 8, r0);
-            tmem_ld8(ta1 + c8 * 8, r1);
-            double cv[8];
+          for (int c4 = 0; c4 < CPT / 4; ++c4) {
+            uint32_t r0[4], r1[4];
+            tmem_ld4(ta0 + c4 * 4, r0);
+            tmem_ld4(ta1 + c4 * 4, r1);
+            double cv[4];
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-              const int col = col0 + c8 * 8 + jj;
+            for (int jj = 0; jj < 4; ++jj) {
+              const int col = col0 + c4 * 4 + jj;
               cv[jj] = (needs_c && rowok && col < a.N) ? a.C[row + (long)col * a.ldc] : 0.0;
             }
             tmem_ld_wait();
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-              const int c = c8 * 8 + jj;
+            for (int jj = 0; jj < 4; ++jj) {
+              const int c = c4 * 4 + jj;
               const int col = col0 + c;
-              const int f = __shfl_sync(0xFFFFFFFFu, fcol[c / 32], c % 32);
+              const int f = __shfl_sync(0xFFFFFFFFu, fcol[0], c);
               if (!rowok || col >= a.N || (a.lower && row < col)) continue;
               const int I = f2i(r0[jj]) + (nj == 2 ? f2i(r1[jj]) : 0);
               double D;
@@ -441,7 +440,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int jj = 0; jj < 8; ++jj) {
             const int c = c8 * 8 + jj;
             const int col = col0 + c;
-            const int f = __shfl_sync(0xFFFFFFFFu, fcol[c / 32], c % 32);
+            const int f = __shfl_sync(0xFFFFFFFFu, fcol[0], c);
             if (!rowok || col >= a.N || (a.lower && row < col)) continue;
             double D;
             if (e_row == kNonFinite || f == kNonFinite)
