@@ -139,6 +139,29 @@ int emul_dpotrs(emul_handle_t h, char uplo, int n, int nrhs, const double* L, in
 int emul_backward_error(emul_handle_t h, int n, const double* A, int lda, const double* x, const double* b,
                         double* out);
 
+/* -------------------------------------------------------- no allocation --
+ * emul_dgemm without any device allocation, for callers that cannot call
+ * cudaMalloc: code that runs while a stream is being captured into a CUDA
+ * graph, or a host library whose device memory is owned by another allocator
+ * (a framework's caching allocator, a memory pool sized at start-up).  The
+ * paper has no counterpart to this entry point.
+ *
+ * Same arguments and results as emul_dgemm, but on `stream` (a cudaStream_t)
+ * instead of a handle.  The scratch (slices, scales, schedule, status word)
+ * lives in one 16 MiB static device array that every GPU which loads this
+ * library holds until the process exits.  Limit: with kp = k rounded up to a
+ * multiple of 8, 2 * slices * kp * (m + n) + 4 * (m + n) + about 17 KB must
+ * fit in 16 MiB, else the call returns EMUL_NO_WORKSPACE and enqueues
+ * nothing.  The first call on a device sets up that device (it looks up the
+ * device address of the array); make that first call before any stream
+ * capture.  Every call reuses the same array and keeps the previous call's
+ * contents: calls that overlap on the GPU (other streams, other threads)
+ * race and give unspecified results.  A device-side wait that gives up is
+ * not reported by this entry point (C is then unspecified).
+ */
+int emul_dgemm_noalloc(void* stream, int m, int n, int k, double alpha, const double* A, int lda, const double* B,
+                       int ldb, double beta, double* C, int ldc, int slices);
+
 /* ------------------------------------------------------------ profiling --
  * Counters of the work this handle enqueued, for benchmarks (no paper
  * counterpart).  While enabled, every launch of the slice-pair product kernel

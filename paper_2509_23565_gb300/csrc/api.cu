@@ -5,6 +5,8 @@
 #include <string>
 #include <vector>
 
+#include <mutex>
+
 #include <cudaTypedefs.h>
 
 #include "handle.h"
@@ -466,3 +468,148 @@ int emul_dgemm(emul_handle_t h, int m, int n, int k, double alpha, const double*
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// emul_dgemm_noalloc: the emulated DGEMM for callers that cannot allocate
+// device memory (for example code running inside a stream capture that must
+// not allocate, or a host library whose allocator is owned by someone else).
+// All scratch lives in one file-scope device array of kNoAllocScratchBytes
+// that every GPU which loads this library keeps until the process exits.
+namespace emul {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;   // 16 MiB
+constexpr size_t kNoAllocSchedBytes = 16384;                // room for 2048 sweeps
+constexpr int kNoAllocMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+struct NoAllocDevice {
+  unsigned char* base = nullptr;   // device address of g_noalloc_scratch on this device
+  int nsm = 0;
+};
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+void* g_noalloc_encode = nullptr;
+std::mutex g_noalloc_mu;
+
+// One-time set-up per device, with that device current: the device address of
+// the static scratch (host code must not use the symbol itself) and the
+// tensor-map encoder.
+int noalloc_setup(int dev, NoAllocDevice** out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  NoAllocDevice& d = g_noalloc_dev[dev];
+  if (!d.base) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return EMUL_CUDA_ERROR;
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return EMUL_CUDA_ERROR;
+    if (!g_noalloc_encode) {
+      cudaDriverEntryPointQueryResult q;
+      if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &g_noalloc_encode, 12000, cudaEnableDefault,
+                                           &q) != cudaSuccess ||
+          q != cudaDriverEntryPointSuccess || !g_noalloc_encode)
+        return EMUL_CUDA_ERROR;
+    }
+    d.base = static_cast<unsigned char*>(ptr);
+    d.nsm = nsm;
+  }
+  *out = &d;
+  return EMUL_OK;
+}
+
+int noalloc_map(CUtensorMap* map, const uint16_t* base, int rows, int k, long kpad, int s, int box_rows) {
+  auto fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(g_noalloc_encode);
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(k), static_cast<cuuint64_t>(rows), static_cast<cuuint64_t>(s)};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(kpad) * 2, static_cast<cuuint64_t>(kpad) * 2 * rows};
+  cuuint32_t box[3] = {static_cast<cuuint32_t>(kBK), static_cast<cuuint32_t>(box_rows), 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<uint16_t*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS
+             ? EMUL_OK
+             : EMUL_CUDA_ERROR;
+}
+
+}  // namespace
+}  // namespace emul
+
+extern "C" int emul_dgemm_noalloc(void* stream, int m, int n, int k, double alpha, const double* A, int lda,
+                                  const double* B, int ldb, double beta, double* C, int ldc, int slices) {
+  using namespace emul;
+  if (m < 0 || n < 0 || k < 0 || slices < 1 || slices > kMaxSlices || lda < (m > 1 ? m : 1) ||
+      ldb < (k > 1 ? k : 1) || ldc < (m > 1 ? m : 1) || (m > 0 && n > 0 && !C) ||
+      (m > 0 && n > 0 && k > 0 && (!A || !B)) || k > 16384 * 4)
+    return EMUL_INVALID_ARG;
+  if (m == 0 || n == 0) return EMUL_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return EMUL_CUDA_ERROR;
+  NoAllocDevice* d = nullptr;
+  int rc = noalloc_setup(dev, &d);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (k == 0) {
+    scale_c_kernel<<<1024, 256, 0, st>>>(m, n, alpha, beta, C, ldc);
+    return cudaGetLastError() == cudaSuccess ? EMUL_OK : EMUL_CUDA_ERROR;
+  }
+  // scratch layout: status word | schedule | row scales | column scales | slices of A | slices of B
+  const long kp = kpad_of(k);
+  const size_t off_sched = kAlign;
+  const size_t off_ea = off_sched + kNoAllocSchedBytes;
+  const size_t off_fb = off_ea + align_up(static_cast<size_t>(m) * 4);
+  const size_t off_sa = off_fb + align_up(static_cast<size_t>(n) * 4);
+  const size_t off_sb = off_sa + align_up(static_cast<size_t>(slices) * m * kp * 2);
+  const size_t need = off_sb + align_up(static_cast<size_t>(slices) * n * kp * 2);
+  if (need > kNoAllocScratchBytes) return EMUL_NO_WORKSPACE;   // operands exceed the 16 MiB static scratch
+
+  unsigned char* base = d->base;
+  int* status = reinterpret_cast<int*>(base);
+  Sweep* sched = reinterpret_cast<Sweep*>(base + off_sched);
+  int32_t* ea = reinterpret_cast<int32_t*>(base + off_ea);
+  int32_t* fb = reinterpret_cast<int32_t*>(base + off_fb);
+  uint16_t* sa = reinterpret_cast<uint16_t*>(base + off_sa);
+  uint16_t* sb = reinterpret_cast<uint16_t*>(base + off_sb);
+
+  const bool wide = !narrow_ok(slices, k);
+  const int nch = (k + kBK - 1) / kBK;
+  std::vector<Sweep> v;
+  if (!build_schedule(slices, nch, wide, v)) return EMUL_INVALID_ARG;
+  if (v.size() * sizeof(Sweep) > kNoAllocSchedBytes) return EMUL_NO_WORKSPACE;
+  // the status word must start at zero; the rest is fully rewritten by this call
+  if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return EMUL_CUDA_ERROR;
+  if (cudaMemcpyAsync(sched, v.data(), v.size() * sizeof(Sweep), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return EMUL_CUDA_ERROR;
+  if (launch_split(st, m, k, A, 1, lda, slices, ea, sa, kp) != cudaSuccess) return EMUL_CUDA_ERROR;
+  if (launch_split(st, n, k, B, ldb, 1, slices, fb, sb, kp) != cudaSuccess) return EMUL_CUDA_ERROR;
+  const int BN = wide ? 64 : 128;
+  CUtensorMap tmA, tmB;
+  rc = noalloc_map(&tmA, sa, m, k, kp, slices, 128);
+  if (rc) return rc;
+  rc = noalloc_map(&tmB, sb, n, k, kp, slices, BN);
+  if (rc) return rc;
+  GemmArgs a{};
+  a.M = m;
+  a.N = n;
+  a.K = k;
+  a.s = slices;
+  a.t = slices + 1;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.C = C;
+  a.ldc = ldc;
+  a.ea = ea;
+  a.fb = fb;
+  a.sched = sched;
+  a.nsweeps = static_cast<int>(v.size());
+  a.tiles_m = (m + 127) / 128;
+  a.tiles_n = (n + BN - 1) / BN;
+  a.ntiles = a.tiles_m * a.tiles_n;
+  a.status = status;
+  a.wait_limit = 2000000000LL;
+  const size_t stage = gemm_stage_bytes(wide, slices);
+  int stages = static_cast<int>((232448 - 1024 - 512) / stage);
+  if (stages > 4) stages = 4;
+  if (stages < 2) return EMUL_NOT_SUPPORTED;
+  const int grid = a.ntiles < d->nsm ? a.ntiles : d->nsm;
+  return launch_gemm(st, wide, tmA, tmB, a, grid, stages, stages * stage + 1024) == cudaSuccess ? EMUL_OK
+                                                                                             : EMUL_CUDA_ERROR;
+}
