@@ -107,13 +107,20 @@ def barrier(world):
 
 
 def max_over_ranks(world, x):
+    """Largest value over the ranks (the slowest rank's time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_value(world, n, steps, ms_max):
+    """Whole-job TFLOP/s of `world` replicas, each factoring one n x n matrix per step."""
+    return world * lu_flops(n) * steps / (ms_max / 1e3) / 1e12
 
 
 def cpu_oracle_lu(n, nb, s, seed):
@@ -215,7 +222,7 @@ def run_ours(args, world, rank, local):
     berr = lib.backward_error(A_chk, xb, b_chk).cpu().numpy()
     info_v = int(info.item())
 
-    value = world * lu_flops(n) * args.steps / (ms_max / 1e3) / 1e12
+    value = aggregate_value(world, n, args.steps, ms_max)
     peaks, peak_kind = measured_peaks()
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
     achieved = prof["product_tensor_flops"] / (prof["product_ms"] / 1e3) / 1e12 if prof["product_ms"] > 0 else 0.0
