@@ -334,13 +334,108 @@ def run_gemm(args):
                                    "frac": ach / peak, "peak_kind": f"bf16 dense burst, {kind}"}}), flush=True)
 
 
+def run_selector(args):
+    """Ablation of the learned slice selector (BASELINE config 4): LU + solve with
+    slices chosen per step by the trained network (plus the a-posteriori probe)
+    against fixed s = 8, on a uniform and on a mixed-range matrix."""
+    import torch
+    from paper_2509_23565_gb300 import inputs
+    from paper_2509_23565_gb300.binding import ColMajor, Emul
+    lib = Emul()
+    lib.selector_load(os.path.join(ROOT, "paper_2509_23565_gb300", "selector_weights.bin"))
+    n, nb = args.n, args.nb
+    out = {"metric": "learned slice selector vs fixed s=8: LU TFLOP/s at backward error <= 16",
+           "config": {"workload": f"LU partial pivoting + solve n={n} nb={nb}", "n": n, "nb": nb}, "cases": {}}
+    for name, A in (("uniform", inputs.uniform(n, n, seed=8100)),
+                    ("mixed_r_0_8_16", inputs.mixed_range(n, nb, (0, 8, 16), seed=8101))):
+        b = inputs.vector(n, seed=8102)
+        A0 = torch.from_numpy(np.ascontiguousarray(A.T)).cuda()
+        b0 = torch.from_numpy(b).cuda()
+        W = ColMajor(torch.empty_like(A0), n, n)
+        x = ColMajor(torch.empty((1, n), dtype=torch.float64, device="cuda"), n, 1)
+        row = {}
+        for label, s in (("fixed_s8", 8), ("learned", 0)):
+            times, st = [], None
+            for rep in range(args.warmup + args.steps):
+                W.store.copy_(A0)
+                x.store[0].copy_(b0)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ipiv, info, st = lib.dgetrf(W, nb=nb, slices=s, stats=True)
+                lib.dgetrs(W, ipiv, x)
+                torch.cuda.synchronize()
+                if rep >= args.warmup:
+                    times.append(time.perf_counter() - t0)
+            be = lib.backward_error(ColMajor(A0, n, n), x, ColMajor(b0.view(1, n), n, 1)).cpu().numpy()
+            t = statistics.median(times)
+            row[label] = {"seconds": t, "tflops": lu_flops(n) / t / 1e12, "backward_error": float(be[1]),
+                          "slices_mean": st.slices_mean, "slices_min": st.slices_min, "slices_max": st.slices_max,
+                          "checks_failed": st.checks_failed}
+        row["speedup"] = row["fixed_s8"]["seconds"] / row["learned"]["seconds"]
+        out["cases"][name] = row
+    print(json.dumps(out), flush=True)
+
+
+def run_batched(args):
+    """BASELINE config 5: many uneven LU solves (n log-uniform in [64, 1024],
+    uniform(-1,1) entries, half of them scaled with r = 8) in one persistent,
+    graph-recorded launch: reduced-slice factorization + FP64 refinement."""
+    import torch
+    from paper_2509_23565_gb300 import inputs
+    from paper_2509_23565_gb300.binding import ColMajor, Emul
+    count = args.batch_count
+    sizes = inputs.batch_sizes(count, 64, 1024, seed=9000)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(9001)
+    As, bs, b0 = [], [], []
+    for i, n in enumerate(sizes):
+        r = 8 if i % 2 else 0
+        As.append(ColMajor(inputs.log_scaled_device(int(n), int(n), r, gen), int(n), int(n)))
+        v = torch.rand(int(n), generator=gen, device="cuda", dtype=torch.float64) * 2 - 1
+        b0.append(v)
+        bs.append(ColMajor(v.clone().view(1, int(n)), int(n), 1))
+    lib = Emul()
+    tune_path = os.path.join(ROOT, "gpurun_out", "batched_autotune.json") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else None
+    t0 = time.perf_counter()
+    lib.autotune(tune_path)
+    t_tune = time.perf_counter() - t0
+    flops = sum(lu_flops(int(n)) for n in sizes)
+    times = []
+    for rep in range(args.warmup + args.steps):
+        for b, v in zip(bs, b0):
+            b.store[0].copy_(v)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        info, berr, iters = lib.dgesv_batched_ir(As, bs, max_iter=30)
+        e1.record()
+        torch.cuda.synchronize()
+        if rep >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+    lib.sync_status()
+    ms = statistics.median(times)
+    be = berr.cpu().numpy()
+    it = iters.cpu().numpy()
+    print(json.dumps({"metric": "batched uneven LU solves TFLOP/s (reduced-slice LU + FP64 refinement)",
+                      "value": flops / (ms / 1e3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ms,
+                      "steps": args.steps, "warmup": args.warmup,
+                      "config": {"workload": f"{count} systems, n log-uniform [64, 1024], r in {{0, 8}}",
+                                 "total_lu_flops": flops},
+                      "max_backward_error": float(be.max()), "mean_iterations": float(it.mean()),
+                      "max_iterations": int(it.max()), "nonzero_info": int((info.cpu().numpy() != 0).sum()),
+                      "autotune_seconds": t_tune}), flush=True)
+
+
 def main():
     p = argparse.ArgumentParser(description=__doc__)
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="lu", choices=["lu", "gemm"])
+    p.add_argument("--workload", default="lu", choices=["lu", "gemm", "selector", "batched"])
+    p.add_argument("--batch-count", type=int, default=4096)
     p.add_argument("--k", type=int, default=256)
     p.add_argument("--n", type=int, default=32768)
     p.add_argument("--nb", type=int, default=256)
@@ -360,6 +455,12 @@ def main():
         return
     if args.workload == "gemm":
         run_gemm(args)
+        return
+    if args.workload == "selector":
+        run_selector(args)
+        return
+    if args.workload == "batched":
+        run_batched(args)
         return
     world, rank, local = dist_setup()
     run_ours(args, world, rank, local)

@@ -23,7 +23,7 @@
  *     on the device: 0 = success, k > 0 = zero pivot / non-SPD leading minor
  *     at 1-based index k.
  *   - `slices` is s, the number of signed 7-bit INT8 slices per operand
- *     (3..8).  The slice products run on tcgen05 tensor cores as integer-valued
+ *     (3..8; emul_dgetrf also accepts 0: chosen per step by the selector).  The slice products run on tcgen05 tensor cores as integer-valued
  *     BF16 with FP32 accumulation that is kept exact (|partial sums| < 2^24).
  *   - Return value: EMUL_OK or a negative status below.  On an error,
  *     emul_last_error(h) gives a one-line reason.  Nothing is enqueued when
@@ -106,6 +106,7 @@ typedef struct emul_stats {
   int slices_max;     /* largest slice count used by a trailing update */
   int checks_failed;  /* a-posteriori checks that triggered a recomputation */
   double seconds;     /* host wall time of the call (set only when it synchronises) */
+  double slices_mean; /* mean slice count over the trailing updates */
 } emul_stats;
 
 /* LU with partial pivoting of the n x n matrix A (lda), in place (Section 4,
@@ -138,6 +139,79 @@ int emul_dpotrs(emul_handle_t h, char uplo, int n, int nrhs, const double* L, in
  * with eps = 2^-53. */
 int emul_backward_error(emul_handle_t h, int n, const double* A, int lda, const double* x, const double* b,
                         double* out);
+
+/* ------------------------------------------------------ batched solves --
+ * Many independent systems A_i x_i = b_i of uneven sizes (1..4096) in one
+ * persistent launch recorded in a CUDA graph (BASELINE config 5): each block
+ * takes whole systems from a work queue (largest first) and factors them in
+ * reduced precision -- FP32 panel with partial pivoting, trailing updates by
+ * the split-integer product (Sec. 2, Eq. 2) with `slices` INT8 slices as exact
+ * INT8 x INT8 -> INT32 dot products -- then refines in FP64 (residual
+ * b - A x with the original A) until the backward error
+ * ||b - A x|| / (||A|| ||x|| n 2^-53) is at most 1 or max_iter is reached.
+ * A system whose refinement has not converged after 8 steps is refactored
+ * with 8 slices (the per-row scales of few slices drop entries far below
+ * their row's largest, the range effect of Sec. 2, Eq. 3), then refined on.
+ *   count        number of systems
+ *   n_arr, lda_arr, A_arr, b_arr   HOST arrays: sizes, leading dimensions,
+ *                device pointers of A_i (n_i x n_i, column-major, not modified)
+ *                and of b_i (overwritten by x_i)
+ *   info_arr, berr_arr, iters_arr  DEVICE arrays of count entries: zero pivot
+ *                index of the FP32 factorization (0 = none), final backward
+ *                error, refinement iterations
+ *   slices       2..8 (first factorization), or 0 = per size bucket from the autotuned table
+ *   nb           16, 32, 64, or 0 = autotuned
+ * The workspace holds one FP32 copy of the largest system per SM. */
+int emul_dgesv_batched_ir(emul_handle_t h, int count, const int* n_arr, double* const* A_arr, const int* lda_arr,
+                          double* const* b_arr, int32_t* info_arr, double* berr_arr, int32_t* iters_arr, int max_iter,
+                          int slices, int nb);
+/* Autotuner of the batched solver: for each size bucket [0,128), [128,256),
+ * [256,512), [512,4096] time every (nb, slices) in {16,32,64} x {3,4} on
+ * synthetic systems and keep the fastest whose refinement passes; the table is
+ * read from `cache_path` (JSON lines) if it exists, else tuned and written
+ * there (NULL: tune, do not cache). */
+int emul_autotune(emul_handle_t h, const char* cache_path);
+
+/* ------------------------------------------------------ slice selector --
+ * A small MLP predicts, per trailing update, the fewest slices that keep the
+ * update within FP64 accuracy (BASELINE config 4; the paper's Sec. 3 cites
+ * a-posteriori validation of error-free products, which the check below
+ * follows).  Features (64 floats): 32-bin histograms of each entry's exponent
+ * offset from its row scale (A) and from its column scale (B), each divided
+ * by its entry count; offsets >= 31 and zeros fall in bin 31.  Network:
+ * 64 -> 128 -> 128 -> 128 -> 6 (ReLU; classes s = 3..8), BF16 weights for the
+ * products, FP32 master weights, FP32 accumulation, softmax cross-entropy,
+ * AdamW.  Parameters are one flat FP32 array of EMUL_SELECTOR_PARAMS values:
+ * W0[128][64], b0[128], W1[128][128], b1[128], W2[128][128], b2[128], W3[6][128], b3[6].
+ * emul_dgetrf with slices = 0 uses the loaded network per step and checks
+ * each update with a Freivalds probe on sampled rows; an update that fails
+ * the probe is redone with 8 slices (counted in emul_stats.checks_failed).
+ */
+#define EMUL_SELECTOR_FEATURES 64
+#define EMUL_SELECTOR_CLASSES 6
+#define EMUL_SELECTOR_PARAMS 42118
+
+/* Features of the product block A (m x k, lda) times B (k x n, ldb); feat: 64 floats (device). */
+int emul_selector_features(emul_handle_t h, int m, int n, int k, const double* A, int lda, const double* B, int ldb,
+                           float* feat);
+/* Training labels: err[s-3] = max_ij |D_s - D_8|_ij / (4 k 2^-53 (|A||B|)_ij) for s = 3..8 (device,
+ * 6 doubles), D_s the emulated product with s slices, all from one INT32 level-sum pass. */
+int emul_slice_errors(emul_handle_t h, int m, int n, int k, const double* A, int lda, const double* B, int ldb,
+                      double* err);
+/* Parameters from / to host memory (EMUL_SELECTOR_PARAMS floats); setting resets the optimizer state. */
+int emul_selector_set_params(emul_handle_t h, const float* params);
+int emul_selector_get_params(emul_handle_t h, float* params);
+/* Gradients of the mean cross-entropy (device, EMUL_SELECTOR_PARAMS floats) and the loss (device, 1 float)
+ * for a batch (<= 8192) of features X (batch x 64, row-major, device) and labels in 3..8 (device). */
+int emul_selector_grad(emul_handle_t h, int batch, const float* X, const int32_t* labels, float* grad, float* loss);
+/* One AdamW step (beta1 0.9, beta2 0.999, eps 1e-8) on a batch; loss (device, may be NULL). */
+int emul_selector_train_step(emul_handle_t h, int batch, const float* X, const int32_t* labels, float lr,
+                             float weight_decay, float* loss);
+/* Predicted slice counts (3..8) for a batch of features (device in, device out). */
+int emul_selector_predict(emul_handle_t h, int batch, const float* X, int32_t* slices);
+/* Weight file: "SEL1", count, then the flat parameters (little-endian FP32). */
+int emul_selector_save(emul_handle_t h, const char* path);
+int emul_selector_load(emul_handle_t h, const char* path);
 
 /* -------------------------------------------------------- no allocation --
  * emul_dgemm without any device allocation, for callers that cannot call

@@ -39,6 +39,17 @@ SIGNATURES = {
     "emul_dpotrf": (_c_int, [_vp, _c_char, _c_int, _vp, _c_int, _c_int, _c_int, _vp, _vp]),
     "emul_dpotrs": (_c_int, [_vp, _c_char, _c_int, _c_int, _vp, _c_int, _vp, _c_int]),
     "emul_backward_error": (_c_int, [_vp, _c_int, _vp, _c_int, _vp, _vp, _vp]),
+    "emul_selector_features": (_c_int, [_vp, _c_int, _c_int, _c_int, _vp, _c_int, _vp, _c_int, _vp]),
+    "emul_slice_errors": (_c_int, [_vp, _c_int, _c_int, _c_int, _vp, _c_int, _vp, _c_int, _vp]),
+    "emul_selector_set_params": (_c_int, [_vp, _vp]),
+    "emul_selector_get_params": (_c_int, [_vp, _vp]),
+    "emul_selector_grad": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp]),
+    "emul_selector_train_step": (_c_int, [_vp, _c_int, _vp, _vp, ctypes.c_float, ctypes.c_float, _vp]),
+    "emul_selector_predict": (_c_int, [_vp, _c_int, _vp, _vp]),
+    "emul_selector_save": (_c_int, [_vp, ctypes.c_char_p]),
+    "emul_selector_load": (_c_int, [_vp, ctypes.c_char_p]),
+    "emul_dgesv_batched_ir": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _c_int, _c_int, _c_int]),
+    "emul_autotune": (_c_int, [_vp, ctypes.c_char_p]),
     "emul_profile_enable": (_c_int, [_vp, _c_int]),
     "emul_profile_read": (_c_int, [_vp, _vp]),
 }
@@ -52,7 +63,7 @@ class EmulError(RuntimeError):
 
 class Stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("slices_min", ctypes.c_int), ("slices_max", ctypes.c_int),
-                ("checks_failed", ctypes.c_int), ("seconds", ctypes.c_double)]
+                ("checks_failed", ctypes.c_int), ("seconds", ctypes.c_double), ("slices_mean", ctypes.c_double)]
 
 
 class Profile(ctypes.Structure):
@@ -205,6 +216,80 @@ class Emul:
     def dpotrs(self, L, B):
         self._check(self.lib.emul_dpotrs(self.h, b"L", L.m, B.n, _vp(L.ptr), L.ld, _vp(B.ptr), B.ld),
                     "emul_dpotrs")
+
+    # ---------------------------------------------------------------- batched
+    def dgesv_batched_ir(self, As, bs, max_iter=10, slices=0, nb=0):
+        """As: list of ColMajor n_i x n_i (not modified); bs: list of ColMajor n_i x 1
+        (overwritten by x_i).  Returns (info, berr, iters) as device tensors."""
+        import torch
+        count = len(As)
+        n_arr = (ctypes.c_int * count)(*[a.m for a in As])
+        lda_arr = (ctypes.c_int * count)(*[a.ld for a in As])
+        A_arr = (ctypes.c_void_p * count)(*[a.ptr for a in As])
+        b_arr = (ctypes.c_void_p * count)(*[b.ptr for b in bs])
+        info = torch.zeros(max(count, 1), dtype=torch.int32, device="cuda")
+        berr = torch.zeros(max(count, 1), dtype=torch.float64, device="cuda")
+        iters = torch.zeros(max(count, 1), dtype=torch.int32, device="cuda")
+        self._check(self.lib.emul_dgesv_batched_ir(self.h, count, n_arr, A_arr, lda_arr, b_arr, _vp(info.data_ptr()),
+                                                   _vp(berr.data_ptr()), _vp(iters.data_ptr()), max_iter, slices, nb),
+                    "emul_dgesv_batched_ir")
+        return info[:count], berr[:count], iters[:count]
+
+    def autotune(self, cache_path=None):
+        self._check(self.lib.emul_autotune(self.h, cache_path.encode() if cache_path else None), "emul_autotune")
+
+    # ---------------------------------------------------------------- selector
+    SELECTOR_PARAMS = 42118
+
+    def selector_features(self, A, B):
+        import torch
+        feat = torch.zeros(64, dtype=torch.float32, device="cuda")
+        self._check(self.lib.emul_selector_features(self.h, A.m, B.n, A.n, _vp(A.ptr), A.ld, _vp(B.ptr), B.ld,
+                                                    _vp(feat.data_ptr())), "emul_selector_features")
+        return feat
+
+    def slice_errors(self, A, B):
+        import torch
+        err = torch.zeros(6, dtype=torch.float64, device="cuda")
+        self._check(self.lib.emul_slice_errors(self.h, A.m, B.n, A.n, _vp(A.ptr), A.ld, _vp(B.ptr), B.ld,
+                                               _vp(err.data_ptr())), "emul_slice_errors")
+        return err
+
+    def selector_set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == self.SELECTOR_PARAMS
+        self._check(self.lib.emul_selector_set_params(self.h, p.ctypes.data_as(_vp)), "emul_selector_set_params")
+
+    def selector_get_params(self):
+        p = np.zeros(self.SELECTOR_PARAMS, dtype=np.float32)
+        self._check(self.lib.emul_selector_get_params(self.h, p.ctypes.data_as(_vp)), "emul_selector_get_params")
+        return p
+
+    def selector_grad(self, X, labels):
+        import torch
+        g = torch.zeros(self.SELECTOR_PARAMS, dtype=torch.float32, device="cuda")
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        self._check(self.lib.emul_selector_grad(self.h, X.shape[0], _vp(X.data_ptr()), _vp(labels.data_ptr()),
+                                                _vp(g.data_ptr()), _vp(loss.data_ptr())), "emul_selector_grad")
+        return g, loss
+
+    def selector_train_step(self, X, labels, lr, weight_decay=0.0, loss=None):
+        self._check(self.lib.emul_selector_train_step(self.h, X.shape[0], _vp(X.data_ptr()), _vp(labels.data_ptr()),
+                                                      lr, weight_decay, _vp(loss.data_ptr() if loss is not None else 0)),
+                    "emul_selector_train_step")
+
+    def selector_predict(self, X):
+        import torch
+        out = torch.zeros(X.shape[0], dtype=torch.int32, device="cuda")
+        self._check(self.lib.emul_selector_predict(self.h, X.shape[0], _vp(X.data_ptr()), _vp(out.data_ptr())),
+                    "emul_selector_predict")
+        return out
+
+    def selector_save(self, path):
+        self._check(self.lib.emul_selector_save(self.h, path.encode()), "emul_selector_save")
+
+    def selector_load(self, path):
+        self._check(self.lib.emul_selector_load(self.h, path.encode()), "emul_selector_load")
 
     def backward_error(self, A, x, b):
         import torch

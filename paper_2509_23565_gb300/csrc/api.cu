@@ -378,6 +378,8 @@ int emul_destroy(emul_handle_t h) {
     cudaEventDestroy(r.e1);
   }
   for (auto ev : h->event_pool) cudaEventDestroy(ev);
+  emul::selector_free(h);
+  emul::batched_free(h);
   if (h->ws) cudaFree(h->ws);
   if (h->d_status) cudaFree(h->d_status);
   delete h;

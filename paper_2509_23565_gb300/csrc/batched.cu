@@ -1,0 +1,604 @@
+// Batched solves of many independent, uneven systems A_i x_i = b_i in one
+// persistent launch (BASELINE config 5), with the split-integer product of
+// arXiv 2509.23565 (Sec. 2, Eq. 2) at a reduced slice count in the LU
+// factorization and FP64 iterative refinement on the residual of Eq. 8.
+//
+// Each block pulls whole systems from an atomic work queue (largest first;
+// no block ever waits on another).  Per system, in the block's scratch:
+//   1. FP32 copy of A; right-looking LU with partial pivoting, block nb:
+//      FP32 panel (pivot = first largest |a|), FP32 triangular solve for U12,
+//      trailing update A22 -= L21 U12 emulated with s INT8 slices: per-row /
+//      per-column power-of-two scales, slices of 7 bits, slice pairs with
+//      p + q <= s + 1 as exact INT8 x INT8 -> INT32 dot products (dp4a),
+//      exact integer recombination, one rounding to FP32;
+//   2. x0 from the FP32 factors; then until the backward error
+//      ||b - A x|| / (||A|| ||x|| n 2^-53) <= target or max_iter: r = b - A x
+//      in FP64 with the original A, d from the FP32 factors, x += d.
+// A and b are not modified; x overwrites b at the end.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
+#include "handle.h"
+
+namespace emul {
+
+struct BatchSys {
+  const double* A;
+  double* b;
+  long lda;
+  int n, nb, s, index;
+};
+
+namespace {
+
+constexpr int kBThreads = 256;
+constexpr int kMaxS = 8;
+constexpr int kStallIters = 8;   // refinement steps before a system is refactored with 8 slices
+
+struct Scratch {
+  float* W;        // n x n (ld n), the FP32 factors
+  int* piv;        // n
+  int8_t* SA;      // [s][n][nb4] slices of L21 rows
+  int8_t* SB;      // [s][n][nb4] slices of U12 columns
+  int* ea;         // n
+  int* fb;         // n
+  double* x;       // n
+  double* r;       // n
+  float* d;        // n
+};
+
+__device__ __forceinline__ int f32_exponent(uint32_t u) {   // smallest e with |x| < 2^e, u = |x| bits (x != 0)
+  const int E = static_cast<int>(u >> 23);
+  if (E > 0) return E - 126;
+  return -118 - __clz(static_cast<int>(u));               // subnormal: |x| = u 2^-149
+}
+
+__device__ __forceinline__ uint64_t f32_scaled(uint32_t u, int e, int W) {   // trunc(|x| 2^(W-e)), < 2^W <= 2^56
+  const int E = static_cast<int>(u >> 23);
+  const uint64_t M = (u & 0x7FFFFFu) | (E ? 0x800000u : 0u);
+  const int sh = (E ? E : 1) - 150 + W - e;
+  if (sh >= 0) return M << sh;                        // sh <= W - 24
+  return -sh >= 64 ? 0ull : (M >> (-sh));
+}
+
+__device__ void block_argmax(float v, int idx, float* sv, int* si, float& bv, int& bi) {
+  // larger |v| wins, ties to the smaller index
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float v2 = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    const int i2 = __shfl_xor_sync(0xFFFFFFFFu, idx, o);
+    if (v2 > v || (v2 == v && i2 < idx)) {
+      v = v2;
+      idx = i2;
+    }
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    sv[w] = v;
+    si[w] = idx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < kBThreads / 32; ++i)
+      if (sv[i] > sv[0] || (sv[i] == sv[0] && si[i] < si[0])) {
+        sv[0] = sv[i];
+        si[0] = si[i];
+      }
+  }
+  __syncthreads();
+  bv = sv[0];
+  bi = si[0];
+  __syncthreads();
+}
+
+__device__ double block_sum_d(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kBThreads / 32; ++i) t += red[i];
+    red[0] = t;
+  }
+  __syncthreads();
+  t = red[0];
+  __syncthreads();
+  return t;
+}
+
+__device__ double block_max_d(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kBThreads / 32; ++i) t = fmax(t, red[i]);
+    red[0] = t;
+  }
+  __syncthreads();
+  t = red[0];
+  __syncthreads();
+  return t;
+}
+
+// Solve (LU) y = P v in FP32 in place on d (length n): row interchanges, unit
+// lower, upper.  Column-oriented, one barrier per column.
+__device__ void lu_solve_f32(const float* W, int n, const int* piv, float* d) {
+  if (threadIdx.x == 0)
+    for (int k = 0; k < n; ++k) {
+      const int p = piv[k];
+      if (p != k) {
+        const float t = d[k];
+        d[k] = d[p];
+        d[p] = t;
+      }
+    }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    const float dk = d[k];
+    for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) d[i] = fmaf(-W[i + static_cast<long>(k) * n], dk, d[i]);
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    if (threadIdx.x == 0) d[k] = d[k] / W[k + static_cast<long>(k) * n];
+    __syncthreads();
+    const float dk = d[k];
+    for (int i = threadIdx.x; i < k; i += blockDim.x) d[i] = fmaf(-W[i + static_cast<long>(k) * n], dk, d[i]);
+    __syncthreads();
+  }
+}
+
+__device__ void factor_system(const BatchSys& S, int s, Scratch& sc, int* info, float* sv, int* si) {
+  const int n = S.n, nb = S.nb;
+  const int nb4 = (nb + 3) / 4 * 4;
+  float* W = sc.W;
+  for (long idx = threadIdx.x; idx < static_cast<long>(n) * n; idx += blockDim.x) {
+    const int i = static_cast<int>(idx % n), j = static_cast<int>(idx / n);
+    W[idx] = static_cast<float>(S.A[i + j * S.lda]);
+  }
+  __syncthreads();
+  for (int j0 = 0; j0 < n; j0 += nb) {
+    const int jb = nb < n - j0 ? nb : n - j0;
+    // ---- panel (FP32, partial pivoting, full-row interchanges)
+    for (int c = j0; c < j0 + jb; ++c) {
+      float bv = -1.f;
+      int bi = 0x7FFFFFFF;
+      for (int r = c + threadIdx.x; r < n; r += blockDim.x) {
+        const float v = fabsf(W[r + static_cast<long>(c) * n]);
+        if (v > bv || (v == bv && r < bi)) {
+          bv = v;
+          bi = r;
+        }
+      }
+      float gv;
+      int p;
+      block_argmax(bv, bi, sv, si, gv, p);
+      if (threadIdx.x == 0) sc.piv[c] = p;
+      if (p != c)
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+          const float t = W[c + static_cast<long>(j) * n];
+          W[c + static_cast<long>(j) * n] = W[p + static_cast<long>(j) * n];
+          W[p + static_cast<long>(j) * n] = t;
+        }
+      __syncthreads();
+      const float piv = W[c + static_cast<long>(c) * n];
+      if (piv == 0.f) {
+        if (threadIdx.x == 0 && *info == 0) *info = c + 1;
+        __syncthreads();
+        continue;
+      }
+      for (int r = c + 1 + threadIdx.x; r < n; r += blockDim.x) {
+        const float l = W[r + static_cast<long>(c) * n] / piv;
+        W[r + static_cast<long>(c) * n] = l;
+        for (int cc = c + 1; cc < j0 + jb; ++cc)
+          W[r + static_cast<long>(cc) * n] = fmaf(-l, W[c + static_cast<long>(cc) * n], W[r + static_cast<long>(cc) * n]);
+      }
+      __syncthreads();
+    }
+    const int m2 = n - j0 - jb;
+    if (m2 <= 0) break;
+    // ---- U12 = L11^-1 A12 (one thread per column)
+    for (int j = j0 + jb + threadIdx.x; j < n; j += blockDim.x)
+      for (int k = j0; k < j0 + jb; ++k) {
+        const float ukj = W[k + static_cast<long>(j) * n];
+        for (int i = k + 1; i < j0 + jb; ++i)
+          W[i + static_cast<long>(j) * n] = fmaf(-W[i + static_cast<long>(k) * n], ukj, W[i + static_cast<long>(j) * n]);
+      }
+    __syncthreads();
+    // ---- scales and slices of L21 (by rows) and U12 (by columns)
+    const int Wb = 7 * s;
+    for (int t = threadIdx.x; t < 2 * m2; t += blockDim.x) {
+      const bool isA = t < m2;
+      const int q = isA ? t : t - m2;
+      uint32_t mx = 0;
+      for (int k = 0; k < jb; ++k) {
+        const float v = isA ? W[(j0 + jb + q) + static_cast<long>(j0 + k) * n] : W[(j0 + k) + static_cast<long>(j0 + jb + q) * n];
+        const uint32_t u = __float_as_uint(v) & 0x7FFFFFFFu;
+        mx = u > mx ? u : mx;
+      }
+      const int e = mx ? f32_exponent(mx) : 0;
+      (isA ? sc.ea : sc.fb)[q] = e;
+      int8_t* dst = (isA ? sc.SA : sc.SB) + static_cast<long>(q) * nb4;
+      for (int k = 0; k < nb4; ++k) {
+        uint32_t u = 0, neg = 0;
+        if (k < jb) {
+          const float v = isA ? W[(j0 + jb + q) + static_cast<long>(j0 + k) * n] : W[(j0 + k) + static_cast<long>(j0 + jb + q) * n];
+          u = __float_as_uint(v);
+          neg = u >> 31;
+          u &= 0x7FFFFFFFu;
+        }
+        const uint64_t mag = u ? f32_scaled(u, e, Wb) : 0ull;
+        for (int pp = 0; pp < s; ++pp) {
+          const int dgt = static_cast<int>((mag >> (7 * (s - 1 - pp))) & 127ull);
+          dst[static_cast<long>(pp) * n * nb4 + k] = static_cast<int8_t>(neg ? -dgt : dgt);
+        }
+      }
+    }
+    __syncthreads();
+    // ---- A22 -= D with D = sum_{L <= s+1} I_L 2^(e_i + f_j - 7L): the level sums I_L
+    // are exact INT32 dot products of INT8 slices (dp4a); they are combined in
+    // FP32, the working precision of this factorization
+    const long ms = static_cast<long>(m2) * m2;
+    const int words = nb4 / 4;
+    for (long idx = threadIdx.x; idx < ms; idx += blockDim.x) {
+      const int i = static_cast<int>(idx % m2), j = static_cast<int>(idx / m2);
+      const int ef = sc.ea[i] + sc.fb[j];
+      float D = 0.f;
+      for (int L = s + 1; L >= 2; --L) {
+        int I = 0;
+        for (int pp = 1; pp <= L - 1; ++pp) {
+          const int qq = L - pp;
+          if (pp > s || qq > s) continue;
+          const int* a = reinterpret_cast<const int*>(sc.SA + (static_cast<long>(pp - 1) * n + i) * nb4);
+          const int* bq = reinterpret_cast<const int*>(sc.SB + (static_cast<long>(qq - 1) * n + j) * nb4);
+          for (int w = 0; w < words; ++w) I = __dp4a(a[w], bq[w], I);
+        }
+        if (I) D += ldexpf(static_cast<float>(I), ef - 7 * L);
+      }
+      float* cp = W + (j0 + jb + i) + static_cast<long>(j0 + jb + j) * n;
+      *cp = *cp - D;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kBThreads) batched_solve_kernel(const BatchSys* sys, int count, unsigned int* queue,
+                                                                  uint8_t* scratch, size_t per_block, int nmax,
+                                                                  int max_iter, double target, int32_t* info_arr,
+                                                                  double* berr_arr, int32_t* iters_arr) {
+  __shared__ float sv[kBThreads / 32];
+  __shared__ int si[kBThreads / 32];
+  __shared__ double red[kBThreads / 32];
+  __shared__ int task_s;
+  __shared__ int info_s;
+  uint8_t* base = scratch + per_block * blockIdx.x;
+  Scratch sc;
+  {
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+      uint8_t* p = base + o;
+      o += (bytes + 255) / 256 * 256;
+      return p;
+    };
+    sc.W = reinterpret_cast<float*>(take(static_cast<size_t>(nmax) * nmax * 4));
+    sc.piv = reinterpret_cast<int*>(take(static_cast<size_t>(nmax) * 4));
+    sc.SA = reinterpret_cast<int8_t*>(take(static_cast<size_t>(kMaxS) * nmax * 64));
+    sc.SB = reinterpret_cast<int8_t*>(take(static_cast<size_t>(kMaxS) * nmax * 64));
+    sc.ea = reinterpret_cast<int*>(take(static_cast<size_t>(nmax) * 4));
+    sc.fb = reinterpret_cast<int*>(take(static_cast<size_t>(nmax) * 4));
+    sc.x = reinterpret_cast<double*>(take(static_cast<size_t>(nmax) * 8));
+    sc.r = reinterpret_cast<double*>(take(static_cast<size_t>(nmax) * 8));
+    sc.d = reinterpret_cast<float*>(take(static_cast<size_t>(nmax) * 4));
+  }
+  while (true) {
+    if (threadIdx.x == 0) task_s = static_cast<int>(atomicAdd(queue, 1u));
+    __syncthreads();
+    const int t = task_s;
+    __syncthreads();
+    if (t >= count) break;
+    const BatchSys S = sys[t];
+    const int n = S.n;
+    if (threadIdx.x == 0) info_s = 0;
+    __syncthreads();
+    int s_cur = S.s;
+    factor_system(S, s_cur, sc, &info_s, sv, si);
+    __syncthreads();
+    // ||A||_inf in FP64
+    double an = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double rs = 0.0;
+      for (int j = 0; j < n; ++j) rs += fabs(S.A[i + j * S.lda]);
+      an = fmax(an, rs);
+    }
+    an = block_max_d(an, red);
+    // x0 from the FP32 factors
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sc.d[i] = static_cast<float>(S.b[i]);
+    __syncthreads();
+    lu_solve_f32(sc.W, n, sc.piv, sc.d);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sc.x[i] = static_cast<double>(sc.d[i]);
+    __syncthreads();
+    double berr = INFINITY;
+    int it = 0;
+    int since = 0;
+    for (;; ++it, ++since) {
+      // r = b - A x (FP64), ||r||, ||x||
+      double rmax = 0.0, xmax = 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double acc = S.b[i];
+        for (int j = 0; j < n; ++j) acc = fma(-S.A[i + j * S.lda], sc.x[j], acc);
+        sc.r[i] = acc;
+        rmax = fmax(rmax, fabs(acc));
+        xmax = fmax(xmax, fabs(sc.x[i]));
+      }
+      rmax = block_max_d(rmax, red);
+      xmax = block_max_d(xmax, red);
+      berr = rmax / (an * xmax * n * 1.1102230246251565e-16);
+      if (!(berr > target) || it >= max_iter || info_s != 0) break;
+      if (since >= kStallIters && s_cur < kMaxS) {
+        // the factors are too coarse for this matrix's range: refactor with 8 slices
+        s_cur = kMaxS;
+        since = 0;
+        factor_system(S, s_cur, sc, &info_s, sv, si);
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) sc.d[i] = static_cast<float>(S.b[i]);
+        __syncthreads();
+        lu_solve_f32(sc.W, n, sc.piv, sc.d);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) sc.x[i] = static_cast<double>(sc.d[i]);
+        __syncthreads();
+        continue;
+      }
+      // d = (LU)^-1 r, computed on r / ||r|| to stay inside FP32 range
+      const double sr = rmax > 0.0 ? rmax : 1.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) sc.d[i] = static_cast<float>(sc.r[i] / sr);
+      __syncthreads();
+      lu_solve_f32(sc.W, n, sc.piv, sc.d);
+      for (int i = threadIdx.x; i < n; i += blockDim.x) sc.x[i] += static_cast<double>(sc.d[i]) * sr;
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) S.b[i] = sc.x[i];
+    if (threadIdx.x == 0) {
+      info_arr[S.index] = info_s;
+      berr_arr[S.index] = berr;
+      iters_arr[S.index] = it;
+    }
+    __syncthreads();
+  }
+}
+
+// --------------------------------------------------------------- autotuning
+struct TuneEntry {
+  int lo, hi, nb, s;
+};
+const int kBucketEdges[] = {0, 128, 256, 512, 1 << 30};
+std::vector<TuneEntry> default_table() {
+  return {{0, 128, 32, 3}, {128, 256, 32, 3}, {256, 512, 32, 3}, {512, 1 << 30, 32, 3}};
+}
+
+}  // namespace
+
+struct BatchedState {
+  std::vector<TuneEntry> table = default_table();
+  bool tuned = false;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t capture = nullptr;   // private stream used only to record the graph
+};
+
+void batched_free(emul_handle_t h) {
+  if (!h->batched) return;
+  BatchedState* st = static_cast<BatchedState*>(h->batched);
+  if (st->exec) cudaGraphExecDestroy(st->exec);
+  if (st->capture) cudaStreamDestroy(st->capture);
+  delete st;
+  h->batched = nullptr;
+}
+
+namespace {
+
+BatchedState* bstate(emul_handle_t h) {
+  if (!h->batched) h->batched = new BatchedState();
+  return static_cast<BatchedState*>(h->batched);
+}
+
+void pick(const BatchedState* st, int n, int& nb, int& s) {
+  for (const auto& e : st->table)
+    if (n >= e.lo && n < e.hi) {
+      nb = e.nb;
+      s = e.s;
+      return;
+    }
+  nb = 32;
+  s = 3;
+}
+
+size_t per_block_bytes(int nmax) {
+  auto a = [](size_t x) { return (x + 255) / 256 * 256; };
+  return a((size_t)nmax * nmax * 4) + a((size_t)nmax * 4) + 2 * a((size_t)kMaxS * nmax * 64) + 2 * a((size_t)nmax * 4) +
+         2 * a((size_t)nmax * 8) + a((size_t)nmax * 4) + 256;
+}
+
+}  // namespace
+
+int batched_run(emul_handle_t h, const std::vector<BatchSys>& sys, int nmax, int32_t* info, double* berr,
+                int32_t* iters, int max_iter, double target) {
+  const int count = static_cast<int>(sys.size());
+  const size_t pb = per_block_bytes(nmax);
+  const int grid = count < h->nsm ? count : h->nsm;
+  const size_t desc_bytes = (count * sizeof(BatchSys) + 255) / 256 * 256;
+  int rc = reserve_workspace(h, desc_bytes + 256 + pb * grid);
+  if (rc) return rc;
+  uint8_t* w = static_cast<uint8_t*>(h->ws);
+  BatchSys* d_sys = reinterpret_cast<BatchSys*>(w);
+  unsigned int* queue = reinterpret_cast<unsigned int*>(w + desc_bytes);
+  uint8_t* scratch = w + desc_bytes + 256;
+  rc = check_cuda(h, cudaMemcpyAsync(d_sys, sys.data(), count * sizeof(BatchSys), cudaMemcpyHostToDevice, h->stream),
+                  "batch descriptors");
+  if (rc) return rc;
+  // one persistent launch, recorded into a CUDA graph together with the queue
+  // reset (on a private stream), then launched on the handle's stream
+  BatchedState* st = bstate(h);
+  if (!st->capture) {
+    rc = check_cuda(h, cudaStreamCreateWithFlags(&st->capture, cudaStreamNonBlocking), "capture stream");
+    if (rc) return rc;
+  }
+  cudaGraph_t graph;
+  rc = check_cuda(h, cudaStreamBeginCapture(st->capture, cudaStreamCaptureModeThreadLocal), "capture");
+  if (rc) return rc;
+  cudaMemsetAsync(queue, 0, sizeof(unsigned int), st->capture);
+  batched_solve_kernel<<<grid, kBThreads, 0, st->capture>>>(d_sys, count, queue, scratch, pb, nmax, max_iter, target,
+                                                            info, berr, iters);
+  rc = check_cuda(h, cudaStreamEndCapture(st->capture, &graph), "capture");
+  if (rc) return rc;
+  if (st->exec) {
+    cudaGraphExecDestroy(st->exec);
+    st->exec = nullptr;
+  }
+  rc = check_cuda(h, cudaGraphInstantiate(&st->exec, graph, 0), "graph instantiate");
+  cudaGraphDestroy(graph);
+  if (rc) return rc;
+  h->launches++;
+  return check_cuda(h, cudaGraphLaunch(st->exec, h->stream), "graph launch");
+}
+
+}  // namespace emul
+
+extern "C" {
+
+int emul_dgesv_batched_ir(emul_handle_t h, int count, const int* n_arr, double* const* A_arr, const int* lda_arr,
+                          double* const* b_arr, int32_t* info_arr, double* berr_arr, int32_t* iters_arr, int max_iter,
+                          int slices, int nb) {
+  if (!h) return EMUL_INVALID_ARG;
+  if (count < 0 || (count > 0 && (!n_arr || !A_arr || !lda_arr || !b_arr || !info_arr || !berr_arr || !iters_arr)) ||
+      max_iter < 0 || !(slices == 0 || (slices >= 2 && slices <= emul::kMaxS)) ||
+      !(nb == 0 || nb == 16 || nb == 32 || nb == 64))
+    return emul::set_error(h, EMUL_INVALID_ARG, "emul_dgesv_batched_ir: invalid argument");
+  if (count == 0) return EMUL_OK;
+  emul::BatchedState* st = emul::bstate(h);
+  std::vector<emul::BatchSys> sys(count);
+  int nmax = 1;
+  for (int i = 0; i < count; ++i) {
+    if (n_arr[i] < 1 || n_arr[i] > 4096 || lda_arr[i] < n_arr[i] || !A_arr[i] || !b_arr[i])
+      return emul::set_error(h, EMUL_INVALID_ARG, "emul_dgesv_batched_ir: invalid system");
+    int tnb, ts;
+    emul::pick(st, n_arr[i], tnb, ts);
+    sys[i] = emul::BatchSys{A_arr[i], b_arr[i], lda_arr[i], n_arr[i], nb ? nb : tnb, slices ? slices : ts, i};
+    nmax = n_arr[i] > nmax ? n_arr[i] : nmax;
+  }
+  // largest systems first so the queue ends with short tasks
+  std::stable_sort(sys.begin(), sys.end(), [](const emul::BatchSys& a, const emul::BatchSys& b) { return a.n > b.n; });
+  return emul::batched_run(h, sys, nmax, info_arr, berr_arr, iters_arr, max_iter, 1.0);
+}
+
+int emul_autotune(emul_handle_t h, const char* cache_path) {
+  if (!h) return EMUL_INVALID_ARG;
+  emul::BatchedState* st = emul::bstate(h);
+  if (cache_path) {
+    std::ifstream in(cache_path);
+    if (in) {
+      std::vector<emul::TuneEntry> t;
+      emul::TuneEntry e;
+      std::string line;
+      while (std::getline(in, line)) {
+        if (sscanf(line.c_str(), " {\"lo\": %d, \"hi\": %d, \"nb\": %d, \"s\": %d}", &e.lo, &e.hi, &e.nb, &e.s) == 4)
+          t.push_back(e);
+      }
+      if (!t.empty()) {
+        st->table = t;
+        st->tuned = true;
+        return EMUL_OK;
+      }
+    }
+  }
+  // time each candidate on a few synthetic systems per size bucket: the fastest
+  // configuration whose refinement reaches the target within 10 iterations wins
+  const int cand_nb[] = {16, 32, 64};
+  const int cand_s[] = {3, 4};
+  const int nb_edges = sizeof(emul::kBucketEdges) / sizeof(int) - 1;
+  std::vector<emul::TuneEntry> table;
+  uint64_t seed = 0x9E3779B97F4A7C15ull;
+  auto rnd = [&]() {   // splitmix64 -> uniform(-1, 1)
+    seed += 0x9E3779B97F4A7C15ull;
+    uint64_t z = seed;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return static_cast<double>(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  };
+  for (int bkt = 0; bkt < nb_edges; ++bkt) {
+    const int lo = emul::kBucketEdges[bkt], hi = emul::kBucketEdges[bkt + 1];
+    const int n = bkt + 1 < nb_edges ? (lo + hi) / 2 : 768;
+    const int count = h->nsm;
+    // one matrix shared by every sample system (the timing is what matters)
+    std::vector<double> hA(static_cast<size_t>(n) * n), hb(static_cast<size_t>(n) * count);
+    for (auto& v : hA) v = rnd();
+    for (auto& v : hb) v = rnd();
+    double *dA = nullptr, *db = nullptr, *dbw = nullptr, *dberr = nullptr;
+    int32_t *dinfo = nullptr, *dit = nullptr;
+    if (cudaMalloc(&dA, hA.size() * 8) != cudaSuccess || cudaMalloc(&db, hb.size() * 8) != cudaSuccess ||
+        cudaMalloc(&dbw, hb.size() * 8) != cudaSuccess || cudaMalloc(&dberr, count * 8) != cudaSuccess ||
+        cudaMalloc(&dinfo, count * 4) != cudaSuccess || cudaMalloc(&dit, count * 4) != cudaSuccess)
+      return emul::set_error(h, EMUL_NO_WORKSPACE, "autotune allocation failed");
+    cudaMemcpy(dA, hA.data(), hA.size() * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy(db, hb.data(), hb.size() * 8, cudaMemcpyHostToDevice);
+    std::vector<int> ns(count, n), lds(count, n);
+    std::vector<double*> As(count), bs(count);
+    for (int i = 0; i < count; ++i) {
+      As[i] = dA;
+      bs[i] = dbw + static_cast<size_t>(i) * n;
+    }
+    float best = 1e30f;
+    emul::TuneEntry be{lo, hi, 32, 3};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int cnb : cand_nb)
+      for (int cs : cand_s) {
+        cudaMemcpy(dbw, db, hb.size() * 8, cudaMemcpyDeviceToDevice);
+        cudaEventRecord(e0, h->stream);
+        int rc = emul_dgesv_batched_ir(h, count, ns.data(), As.data(), lds.data(), bs.data(), dinfo, dberr, dit, 10,
+                                       cs, cnb);
+        cudaEventRecord(e1, h->stream);
+        if (rc) return rc;
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        std::vector<double> be_h(count);
+        cudaMemcpy(be_h.data(), dberr, count * 8, cudaMemcpyDeviceToHost);
+        bool ok = true;
+        for (double v : be_h) ok = ok && v <= 16.0;
+        if (ok && ms < best) {
+          best = ms;
+          be = emul::TuneEntry{lo, hi, cnb, cs};
+        }
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(dA);
+    cudaFree(db);
+    cudaFree(dbw);
+    cudaFree(dberr);
+    cudaFree(dinfo);
+    cudaFree(dit);
+    table.push_back(be);
+  }
+  st->table = table;
+  st->tuned = true;
+  if (cache_path) {
+    std::ofstream out(cache_path);
+    out << "[\n";
+    for (size_t i = 0; i < table.size(); ++i)
+      out << " {\"lo\": " << table[i].lo << ", \"hi\": " << table[i].hi << ", \"nb\": " << table[i].nb
+          << ", \"s\": " << table[i].s << "}" << (i + 1 < table.size() ? ",\n" : "\n");
+    out << "]\n";
+  }
+  return EMUL_OK;
+}
+
+}  // extern "C"

@@ -25,6 +25,7 @@
 
 #include "emul_internal.h"
 #include "ptx.cuh"
+#include "round.cuh"
 
 namespace emul {
 
@@ -50,33 +51,6 @@ struct Cfg {
   using State = typename std::conditional<WIDE, __int128, long long>::type;
 };
 
-// Correctly rounded double of T * 2^sh (round to nearest even), computed with
-// integer operations on the IEEE-754 fields (overflow gives +-inf, results
-// below the normal range are rounded as subnormals).
-__device__ __noinline__ double rn_scaled(__int128 T, int sh) {
-  if (T == 0) return 0.0;
-  const bool neg = T < 0;
-  const unsigned __int128 mag = neg ? (unsigned __int128)(-(T + 1)) + 1u : (unsigned __int128)T;
-  const uint64_t hi = (uint64_t)(mag >> 64), lo = (uint64_t)mag;
-  const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
-  const int E = msb + sh;
-  const uint64_t sign = neg ? 0x8000000000000000ull : 0ull;
-  if (E > 1023) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
-  const int keep = (E >= -1022) ? msb - 52 : -1074 - sh;   // bit of mag kept as the last mantissa bit
-  uint64_t q;
-  if (keep <= 0) {
-    q = (uint64_t)(mag << (-keep));
-  } else {
-    if (keep > msb + 1) return __longlong_as_double((long long)sign);   // below half the smallest subnormal
-    q = (uint64_t)(mag >> keep);
-    const unsigned __int128 rem = mag - ((unsigned __int128)q << keep);
-    const unsigned __int128 half = (unsigned __int128)1 << (keep - 1);
-    if (rem > half || (rem == half && (q & 1ull))) q += 1;
-  }
-  const uint64_t bits = (E >= -1022) ? ((uint64_t)(E + 1022) << 52) + q : q;
-  return __longlong_as_double((long long)(sign | bits));
-}
-
 // Fast path of rn_scaled for T = R * 2^7 + I with |R| < 2^56 and |I| < 2^26
 // (the narrow variant), where |T| < 2^64 fits an unsigned 64-bit magnitude.
 // Results outside the normal exponent range take the generic path.
@@ -100,6 +74,28 @@ __device__ __forceinline__ double rn_scaled_r7(long long R, int I, int sh) {
   const unsigned long long q = (nrm >> 11) + ((rb + 0x3FFull + ((nrm >> 11) & 1ull)) >> 11);
   const unsigned long long bits = ((unsigned long long)(E + 1022) << 52) + q;
   return __longlong_as_double((long long)(bits | (neg ? 0x8000000000000000ull : 0ull)));
+}
+
+// v * 2^e2 as a double, exact, for 0 < |v| < 2^53 and a normal result.
+__device__ __forceinline__ double exact_i64(long long v, int e2) {
+  const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  const int msb = 63 - __clzll((long long)a);
+  const unsigned long long mant = a << (52 - msb);                  // leading one at bit 52
+  const unsigned long long bits = ((unsigned long long)(msb + e2 + 1022) << 52) + mant;
+  return __longlong_as_double((long long)(bits | (v < 0 ? 0x8000000000000000ull : 0ull)));
+}
+
+// RN(T * 2^sh) for T = R * 2^7 + I (|R| < 2^62, |I| < 2^26): T = A1 2^35 + A0 with
+// |A1| < 2^35 and |A0| < 2^37 both exact in FP64, so one DADD of the two exact
+// parts gives the single correct rounding.  Outside -1022 <= sh <= 950 (parts
+// that could be subnormal or overflow) the integer path is used.
+__device__ __forceinline__ double rn_split(long long R, int I, int sh) {
+  if (sh < -1022 || sh > 950) return rn_scaled((__int128)R * 128 + (__int128)I, sh);
+  const long long A1 = R >> 28;
+  const long long A0 = ((R & ((1ll << 28) - 1)) << 7) + I;
+  const double dh = A1 ? exact_i64(A1, sh + 35) : 0.0;
+  const double dl = A0 ? exact_i64(A0, sh) : 0.0;
+  return __dadd_rn(dh, dl);
 }
 
 __device__ __forceinline__ int f2i(uint32_t r) { return __float2int_rn(__uint_as_float(r)); }
@@ -367,7 +363,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               else if (WIDE)
                 D = rn_scaled((__int128)R[c] * 128 + (__int128)I, e_row + f + sh0);
               else
-                D = rn_scaled_r7((long long)R[c], I, e_row + f + sh0);
+                D = rn_split((long long)R[c], I, e_row + f + sh0);
               a.C[row + (long)col * a.ldc] = apply_update<UPD>(a, D, cv[jj]);
             }
           }

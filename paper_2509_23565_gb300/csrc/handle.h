@@ -32,6 +32,8 @@ struct emul_handle_s {
   };
   std::vector<ProfRec> recs;
   std::vector<cudaEvent_t> event_pool;
+  void* selector = nullptr;         // emul::SelectorState (selector.cu)
+  void* batched = nullptr;          // emul::BatchedState (batched.cu)
 };
 
 namespace emul {
@@ -56,5 +58,14 @@ size_t gemm_workspace_bytes(int m, int n, int k, int s, bool same_operand);
 // products back to back on one stream may share offset 0).
 int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Operand B, double beta, double* C,
              long ldc, int s, bool lower, int mode, int32_t* levels, long ldl, long ldl_plane, size_t ws_offset = 0);
+
+// Learned slice selector (selector.cu).
+int selector_features(emul_handle_t h, int m, int n, int k, Operand A, Operand B, float* feat);
+int selector_predict(emul_handle_t h, int batch, const float* X, int32_t* out);
+bool selector_loaded(emul_handle_t h);
+float* selector_feature_buffer(emul_handle_t h);
+int32_t* selector_pred_buffer(emul_handle_t h);
+void selector_free(emul_handle_t h);
+void batched_free(emul_handle_t h);
 
 }  // namespace emul

@@ -449,6 +449,95 @@ __global__ void residual_finish_kernel(int n, const unsigned long long* acc, dou
   out[1] = r / (an * xn * n * eps);
 }
 
+// ------------------------------------------------------------------ a-posteriori probe
+// Freivalds-style check of one trailing update C <- C - L U on sampled rows:
+// with w_j = +-1, (C_old - C_new) w must equal L (U w) up to the emulation
+// tolerance 4 k u (|L||U|)|w| plus FP64 rounding of the three products.
+constexpr int kProbeRows = 64;
+
+__device__ __forceinline__ double probe_w(int j) {
+  unsigned x = static_cast<unsigned>(j) * 2654435761u;
+  x ^= x >> 13;
+  x *= 0x5bd1e995u;
+  x ^= x >> 15;
+  return (x & 1u) ? 1.0 : -1.0;
+}
+
+__device__ __forceinline__ void block_sum2(double& a, double& b) {
+  __shared__ double ra[32], rb[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+    b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    ra[w] = a;
+    rb[w] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a = 0.0;
+    b = 0.0;
+    for (int i = 0; i < static_cast<int>(blockDim.x / 32); ++i) {
+      a += ra[i];
+      b += rb[i];
+    }
+  }
+}
+
+// y[i] = sum_j C(r_i, j) w_j, a[i] = sum_j |C(r_i, j)|, r_i = i*m/R (one block per sampled row)
+__global__ void probe_rows_kernel(int m, int n, const double* C, long ldc, int R, double* y, double* a) {
+  const int i = blockIdx.x;
+  const int r = static_cast<int>(static_cast<long>(i) * m / R);
+  double sy = 0.0, sa = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double c = C[r + static_cast<long>(j) * ldc];
+    sy = fma(c, probe_w(j), sy);
+    sa += fabs(c);
+  }
+  block_sum2(sy, sa);
+  if (threadIdx.x == 0) {
+    y[i] = sy;
+    a[i] = sa;
+  }
+}
+
+// z[q] = sum_j U(q, j) w_j, za[q] = sum_j |U(q, j)| (one block per row q of U, jb x n)
+__global__ void probe_z_kernel(int n, const double* U, long ldu, double* z, double* za) {
+  const int q = blockIdx.x;
+  double sz = 0.0, sa = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double u = U[q + static_cast<long>(j) * ldu];
+    sz = fma(u, probe_w(j), sz);
+    sa += fabs(u);
+  }
+  block_sum2(sz, sa);
+  if (threadIdx.x == 0) {
+    z[q] = sz;
+    za[q] = sa;
+  }
+}
+
+// t[i] = sum_q L(r_i, q) z[q], ta[i] = sum_q |L(r_i, q)| za[q]; then the check (one thread per row)
+__global__ void probe_check_kernel(int m, int n, int k, const double* L, long ldl, int R, const double* z,
+                                   const double* za, const double* y0, const double* a0, const double* y1,
+                                   const double* a1, int* flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= R) return;
+  const int r = static_cast<int>(static_cast<long>(i) * m / R);
+  double t = 0.0, ta = 0.0;
+  for (int q = 0; q < k; ++q) {
+    const double l = L[r + static_cast<long>(q) * ldl];
+    t = fma(l, z[q], t);
+    ta = fma(fabs(l), za[q], ta);
+  }
+  const double u = 1.1102230246251565e-16;
+  const double tol = 6.0 * k * u * ta + 3.0 * n * u * (a0[i] + a1[i]);
+  const double diff = fabs((y0[i] - y1[i]) - t);
+  if (!(diff <= tol)) atomicExch(flag, 1);
+}
+
 // ------------------------------------------------------------------ host helpers
 struct LuBufs {
   double* inv;          // nb x nb
@@ -459,13 +548,16 @@ struct LuBufs {
   GridBar* bar;
   unsigned long long* racc;
   int* map;             // laswp gather maps, [4*kPermMax + 1] ints each, one per recursion depth
+  double* probe;        // y0, a0, y1, a1 (kProbeRows each), z, za (nb each)
+  int* flag;
 };
 constexpr int kMapInts = 4 * kPermMax + 8;
 constexpr int kMaxDepth = 8;
 
 size_t lu_extra_bytes(int nb, int nsm) {
   return al(static_cast<size_t>(nb) * nb * 8) + al(2ull * nsm * kLeaf * 8) + al(2ull * nsm * 8) + al(2ull * nsm * 4) +
-         al(2ull * kLeaf * 8) + al(sizeof(GridBar)) + al(4 * 8) + al(kMaxDepth * kMapInts * 4) + kAl;
+         al(2ull * kLeaf * 8) + al(sizeof(GridBar)) + al(4 * 8) + al(kMaxDepth * kMapInts * 4) +
+         al((4ull * kProbeRows + 2ull * nb) * 8) + al(16) + kAl;
 }
 
 LuBufs carve(emul_handle_t h, size_t off, int nb) {
@@ -486,6 +578,10 @@ LuBufs carve(emul_handle_t h, size_t off, int nb) {
   b.racc = reinterpret_cast<unsigned long long*>(p);
   p += al(4 * 8);
   b.map = reinterpret_cast<int*>(p);
+  p += al(kMaxDepth * kMapInts * 4);
+  b.probe = reinterpret_cast<double*>(p);
+  p += al((4ull * kProbeRows + 2ull * nb) * 8);
+  b.flag = reinterpret_cast<int*>(p);
   return b;
 }
 
@@ -589,20 +685,27 @@ int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int n
                 emul_stats* stats) {
   if (!h) return EMUL_INVALID_ARG;
   if (nb == 0) nb = 128;
-  if (n < 0 || lda < (n > 1 ? n : 1) || nb < 16 || nb > 256 || nb % 16 != 0 || slices < 1 ||
+  if (n < 0 || lda < (n > 1 ? n : 1) || nb < 16 || nb > 256 || nb % 16 != 0 || slices < 0 ||
       slices > emul::kMaxSlices || (n > 0 && (!A || !ipiv || !info)))
     return emul::set_error(h, EMUL_INVALID_ARG, "emul_dgetrf: invalid argument");
-  if (stats) *stats = emul_stats{0, slices, slices, 0, 0.0};
+  const bool autos = slices == 0;
+  if (autos && !emul::selector_loaded(h))
+    return emul::set_error(h, EMUL_INVALID_ARG, "emul_dgetrf: slices = 0 needs a loaded selector");
+  if (stats) *stats = emul_stats{0, autos ? 8 : slices, autos ? 3 : slices, 0, 0.0, 0.0};
+  double slices_sum = 0.0;
+  int updates = 0;
   if (n == 0) return EMUL_OK;
+  const int s_fixed = autos ? 8 : slices;
+  int s_prev = 8;   // auto mode: the panel and U12 use the previous update's slice count
   int rc = emul::check_cuda(h, cudaMemsetAsync(info, 0, sizeof(int32_t), h->stream), "info reset");
   if (rc) return rc;
-  const size_t gw = emul::gemm_workspace_bytes(n, n, nb, slices, false);
+  const size_t gw = emul::gemm_workspace_bytes(n, n, nb, s_fixed, false);
   rc = emul::reserve_workspace(h, gw + emul::lu_extra_bytes(nb, h->nsm));
   if (rc) return rc;
   const emul::LuBufs B = emul::carve(h, gw, nb);
   for (int j0 = 0; j0 < n; j0 += nb) {
     const int jb = nb < n - j0 ? nb : n - j0;
-    rc = emul::rgetrf(h, A, lda, n, j0, jb, ipiv, info, slices, B);
+    rc = emul::rgetrf(h, A, lda, n, j0, jb, ipiv, info, autos ? s_prev : s_fixed, B);
     if (rc) return rc;
     rc = emul::laswp_prepare(h, ipiv, j0, j0 + jb, B.map);
     if (rc) return rc;
@@ -618,17 +721,80 @@ int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int n
       if (rc) return rc;
       double* A12 = A + j0 + static_cast<long>(j0 + jb) * lda;
       // U12 = L11^-1 A12 (jb x m2), written over A12
-      rc = emul::gemm_run(h, jb, m2, jb, 1.0, Operand{B.inv, 1, jb}, Operand{A12, lda, 1}, 0.0, A12, lda, slices,
-                          false, 0, nullptr, 0, 0);
+      rc = emul::gemm_run(h, jb, m2, jb, 1.0, Operand{B.inv, 1, jb}, Operand{A12, lda, 1}, 0.0, A12, lda,
+                          autos ? s_prev : s_fixed, false, 0, nullptr, 0, 0);
       if (rc) return rc;
+      const double* L21 = A + (j0 + jb) + static_cast<long>(j0) * lda;
+      double* A22 = A + (j0 + jb) + static_cast<long>(j0 + jb) * lda;
+      int s_step = slices;
+      if (autos) {
+        // slice count of this update from the selector, then the probe's "before" sums
+        rc = emul::selector_features(h, m2, m2, jb, Operand{L21, 1, lda}, Operand{A12, lda, 1},
+                                     emul::selector_feature_buffer(h));
+        if (rc) return rc;
+        rc = emul::selector_predict(h, 1, emul::selector_feature_buffer(h), emul::selector_pred_buffer(h));
+        if (rc) return rc;
+        int32_t sp = 8;
+        rc = emul::check_cuda(h, cudaMemcpyAsync(&sp, emul::selector_pred_buffer(h), 4, cudaMemcpyDeviceToHost,
+                                                 h->stream), "selector read");
+        if (rc) return rc;
+        rc = emul::check_cuda(h, cudaStreamSynchronize(h->stream), "selector read");
+        if (rc) return rc;
+        s_step = sp < 3 ? 3 : (sp > 8 ? 8 : sp);
+        const int R = m2 < emul::kProbeRows ? m2 : emul::kProbeRows;
+        double* y0 = B.probe;
+        double* a0 = y0 + emul::kProbeRows;
+        double* z = y0 + 4 * emul::kProbeRows;
+        double* za = z + nb;
+        emul::probe_rows_kernel<<<R, 256, 0, h->stream>>>(m2, m2, A22, lda, R, y0, a0);
+        emul::probe_z_kernel<<<jb, 256, 0, h->stream>>>(m2, A12, lda, z, za);
+        h->launches += 2;
+        cudaMemsetAsync(B.flag, 0, sizeof(int), h->stream);
+      }
       // A22 -= L21 U12
-      rc = emul::gemm_run(h, m2, m2, jb, -1.0, Operand{A + (j0 + jb) + static_cast<long>(j0) * lda, 1, lda},
-                          Operand{A12, lda, 1}, 1.0, A + (j0 + jb) + static_cast<long>(j0 + jb) * lda, lda, slices,
+      rc = emul::gemm_run(h, m2, m2, jb, -1.0, Operand{L21, 1, lda}, Operand{A12, lda, 1}, 1.0, A22, lda, s_step,
                           false, 0, nullptr, 0, 0);
       if (rc) return rc;
+      if (autos) {
+        const int R = m2 < emul::kProbeRows ? m2 : emul::kProbeRows;
+        double* y0 = B.probe;
+        double* a0 = y0 + emul::kProbeRows;
+        double* y1 = a0 + emul::kProbeRows;
+        double* a1 = y1 + emul::kProbeRows;
+        double* z = y0 + 4 * emul::kProbeRows;
+        double* za = z + nb;
+        emul::probe_rows_kernel<<<R, 256, 0, h->stream>>>(m2, m2, A22, lda, R, y1, a1);
+        emul::probe_check_kernel<<<(R + 63) / 64, 64, 0, h->stream>>>(m2, m2, jb, L21, lda, R, z, za, y0, a0, y1,
+                                                                       a1, B.flag);
+        h->launches += 2;
+        int fl = 0;
+        rc = emul::check_cuda(h, cudaMemcpyAsync(&fl, B.flag, 4, cudaMemcpyDeviceToHost, h->stream), "probe read");
+        if (rc) return rc;
+        rc = emul::check_cuda(h, cudaStreamSynchronize(h->stream), "probe read");
+        if (rc) return rc;
+        if (fl && s_step < 8) {
+          // undo with the same slice count, redo with 8
+          rc = emul::gemm_run(h, m2, m2, jb, 1.0, Operand{L21, 1, lda}, Operand{A12, lda, 1}, 1.0, A22, lda, s_step,
+                              false, 0, nullptr, 0, 0);
+          if (rc) return rc;
+          rc = emul::gemm_run(h, m2, m2, jb, -1.0, Operand{L21, 1, lda}, Operand{A12, lda, 1}, 1.0, A22, lda, 8,
+                              false, 0, nullptr, 0, 0);
+          if (rc) return rc;
+          if (stats) stats->checks_failed++;
+          s_step = 8;
+        }
+        if (stats) {
+          stats->slices_min = s_step < stats->slices_min ? s_step : stats->slices_min;
+          stats->slices_max = s_step > stats->slices_max ? s_step : stats->slices_max;
+        }
+      }
+      slices_sum += s_step;
+      updates++;
+      s_prev = s_step;
     }
     if (stats) stats->steps++;
   }
+  if (stats) stats->slices_mean = updates ? slices_sum / updates : static_cast<double>(s_fixed);
   return EMUL_OK;
 }
 
@@ -673,7 +839,7 @@ int emul_dpotrf(emul_handle_t h, char uplo, int n, double* A, int lda, int nb, i
   if ((uplo != 'L' && uplo != 'l') || n < 0 || lda < (n > 1 ? n : 1) || nb < 16 || nb > 256 || nb % 16 != 0 ||
       slices < 1 || slices > emul::kMaxSlices || (n > 0 && (!A || !info)))
     return emul::set_error(h, EMUL_INVALID_ARG, "emul_dpotrf: invalid argument");
-  if (stats) *stats = emul_stats{0, slices, slices, 0, 0.0};
+  if (stats) *stats = emul_stats{0, slices, slices, 0, 0.0, static_cast<double>(slices)};
   if (n == 0) return EMUL_OK;
   int rc = emul::check_cuda(h, cudaMemsetAsync(info, 0, sizeof(int32_t), h->stream), "info reset");
   if (rc) return rc;

@@ -90,3 +90,29 @@ def batch_sizes(count, lo, hi, seed):
     """Log-uniform integer sizes in [lo, hi] for the batched solver."""
     rng = _rng(seed)
     return np.floor(np.exp(rng.uniform(np.log(lo), np.log(hi + 1), count))).astype(np.int64).clip(lo, hi)
+
+
+def log_scaled_device(m, n, r, gen, device="cuda"):
+    """u * 10**e (u ~ U(-1, 1), e ~ U(-r, r)) drawn on the device with a seeded
+    torch.Generator; returned as a column-major store (n x m tensor: row j is
+    column j).  Used for bulk training data of the slice selector."""
+    import torch
+    u = torch.rand((n, m), generator=gen, device=device, dtype=torch.float64) * 2.0 - 1.0
+    if r == 0:
+        return u
+    e = (torch.rand((n, m), generator=gen, device=device, dtype=torch.float64) * 2.0 - 1.0) * r
+    return u * torch.pow(10.0, e)
+
+
+def mixed_range(n, nb, ranges, seed):
+    """Uniform(-1, 1) matrix whose block rows (nb rows each) are scaled
+    entrywise by 10**e, e ~ U(-r, r), with r drawn per block row from `ranges`
+    (BASELINE config 4: mixed blocks r in {0, 8, 16})."""
+    rng = _rng(seed)
+    A = rng.random((n, n)) * 2.0 - 1.0
+    for i0 in range(0, n, nb):
+        r = ranges[rng.integers(len(ranges))]
+        if r:
+            rows = slice(i0, min(n, i0 + nb))
+            A[rows, :] *= np.power(10.0, (rng.random((A[rows, :].shape)) * 2.0 - 1.0) * r)
+    return np.asfortranarray(A)
