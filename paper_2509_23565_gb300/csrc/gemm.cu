@@ -37,6 +37,7 @@ constexpr int kLowRegs = 64;            // producer warpgroup after setmaxnreg.d
 constexpr int kHighRegs = 104;          // epilogue warpgroups: 128*64 + 512*104 = 61440
 constexpr int kSlots = 4;
 constexpr int kEpiWarps = 16;
+constexpr int kSchedSmem = 128;
 constexpr int kMaxStages = 4;
 constexpr int kStatusTimeout = -4;
 
@@ -50,31 +51,6 @@ struct Cfg {
   static constexpr uint32_t TMEM_COLS = kSlots * BN;
   using State = typename std::conditional<WIDE, __int128, long long>::type;
 };
-
-// Fast path of rn_scaled for T = R * 2^7 + I with |R| < 2^56 and |I| < 2^26
-// (the narrow variant), where |T| < 2^64 fits an unsigned 64-bit magnitude.
-// Results outside the normal exponent range take the generic path.
-__device__ __forceinline__ double rn_scaled_r7(long long R, int I, int sh) {
-  const bool rneg = R < 0;
-  const unsigned long long aR = rneg ? 0ull - (unsigned long long)R : (unsigned long long)R;
-  if (aR >> 56) return rn_scaled((__int128)R * 128 + (__int128)I, sh);   // |T| may exceed 2^63
-  const long long Is = rneg ? -(long long)I : (long long)I;
-  unsigned long long u = (aR << 7) + (unsigned long long)Is;
-  bool neg = rneg;
-  if (aR < (1ull << 17) && (long long)u < 0) {   // small R: the sum may change sign
-    u = 0ull - u;
-    neg = !neg;
-  }
-  if (u == 0ull) return 0.0;
-  const int lz = __clzll((long long)u);
-  const int E = 63 - lz + sh;
-  if (E < -1022 || E > 1023) return rn_scaled((__int128)R * 128 + (__int128)I, sh);
-  const unsigned long long nrm = u << lz;                     // leading one at bit 63
-  const unsigned long long rb = nrm & 0x7FFull;               // bits below the 53-bit mantissa
-  const unsigned long long q = (nrm >> 11) + ((rb + 0x3FFull + ((nrm >> 11) & 1ull)) >> 11);
-  const unsigned long long bits = ((unsigned long long)(E + 1022) << 52) + q;
-  return __longlong_as_double((long long)(bits | (neg ? 0x8000000000000000ull : 0ull)));
-}
 
 // v * 2^e2 as a double, exact, for 0 < |v| < 2^53 and a normal result.
 __device__ __forceinline__ double exact_i64(long long v, int e2) {
@@ -159,12 +135,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ __align__(8) uint64_t slot_full[kSlots], slot_empty[kSlots], mma_done;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
+  __shared__ Sweep sched_s[kSchedSmem];   // the schedule, when it is short enough
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int s = a.s;
   const uint32_t stage_bytes = (uint32_t)s * (Cf::A_TILE + Cf::B_TILE);
   volatile int* abortp = &abort_flag;
 
+  const bool sched_in_smem = a.nsweeps <= kSchedSmem;
+  if (sched_in_smem)
+    for (int i = threadIdx.x; i < a.nsweeps; i += blockDim.x) sched_s[i] = a.sched[i];
+  const Sweep* sched = sched_in_smem ? sched_s : a.sched;
   if (threadIdx.x == 0) {
     for (int i = 0; i < stages; ++i) {
       mbar_init(&stage_full[i], 1);
@@ -198,7 +179,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tile_coords(a, tile, tm, tn);
         const int m0 = tm * Cf::BM, n0 = tn * Cf::BN;
         for (int sw = 0; sw < a.nsweeps && ok; ++sw) {
-          const Sweep S = a.sched[sw];
+          const Sweep S = sched[sw];
           for (int kc = S.k0c; kc < S.k1c; ++kc, ++it) {
             const int st = (int)(it % stages);
             const uint32_t par = (uint32_t)((it / stages) & 1) ^ 1u;
@@ -230,7 +211,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
         for (int sw = 0; sw < a.nsweeps && ok; ++sw) {
-          const Sweep S = a.sched[sw];
+          const Sweep S = sched[sw];
           const int nj = S.L[1] ? 2 : 1;
           uint32_t dcol[2];
           for (int j = 0; j < nj; ++j) {
@@ -318,7 +299,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int prevL = -1;
       bool held_final = false;
       for (int sw = 0; sw < a.nsweeps && ok; ++sw) {
-        const Sweep S = a.sched[sw];
+        const Sweep S = sched[sw];
         const int nj = S.L[1] ? 2 : 1;
         if (S.held && a.mode == 0) {
           // final step: T = R * 2^7 + (sum of the held jobs of the last level),
