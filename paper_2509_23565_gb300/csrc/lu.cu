@@ -32,26 +32,22 @@ constexpr size_t kAl = 256;
 inline size_t al(size_t x) { return (x + kAl - 1) / kAl * kAl; }
 
 struct GridBar {
-  unsigned count;
-  unsigned gen;
+  unsigned long long count;   // arrivals since the launch (zeroed before it)
 };
 
-// Bounded grid-wide barrier for a cooperative launch of G blocks.
-__device__ bool grid_sync(GridBar* gb, unsigned G, long long limit, int* status) {
+// Bounded grid-wide barrier for a cooperative launch of G blocks on a
+// monotonic arrival counter: barrier number i completes when the counter
+// reaches target = (i + 1) G, so no reset is needed between barriers.
+__device__ bool grid_sync(GridBar* gb, unsigned long long target, long long limit, int* status) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = &gb->gen;
-    const unsigned g = *vgen;
     __threadfence();
     bool ok = true;
-    if (atomicAdd(&gb->count, 1u) == G - 1) {
-      atomicExch(&gb->count, 0u);
-      __threadfence();
-      atomicAdd(&gb->gen, 1u);
-    } else {
+    if (atomicAdd(&gb->count, 1ull) + 1 < target) {
+      volatile unsigned long long* vc = &gb->count;
       const long long t0 = clock64();
-      while (*vgen == g) {
+      while (*vc < target) {
         if (clock64() - t0 > limit) {
           ok = false;
           atomicExch(status, kStatusTimeout);
@@ -78,9 +74,15 @@ __device__ __forceinline__ bool better(uint64_t v1, int r1, uint64_t v2, int r2)
 
 // Leaf panel: rows d0..n-1, columns d0..d0+w-1 of A, factored in place with
 // partial pivoting.  Block b keeps panel rows [b*R, b*R+R) in shared memory.
+// Every interchange is also applied to the columns [pc0, d0) and
+// [d0+w, pc1) of the enclosing panel, which live in global memory: the
+// outside column q (0-based over both ranges) belongs to thread q / G of block
+// q % G for the whole launch, so successive interchanges of one element stay
+// in program order.  Its loads are issued when the pivot is known and its
+// stores at the next column, off the critical path.
 __global__ void __launch_bounds__(kLeafThreads) getf2_leaf_kernel(double* A, long lda, int n, int d0, int w, int R,
-                                                                 int32_t* ipiv, int32_t* info, GridBar* gb,
-                                                                 double* cand_rows, uint64_t* cand_val,
+                                                                 int pc0, int pc1, int32_t* ipiv, int32_t* info,
+                                                                 GridBar* gb, double* cand_rows, uint64_t* cand_val,
                                                                  int* cand_idx, double* diag_rows, int* status,
                                                                  long long limit) {
   extern __shared__ double P[];   // P[c*R + lr]
@@ -89,15 +91,27 @@ __global__ void __launch_bounds__(kLeafThreads) getf2_leaf_kernel(double* A, lon
   __shared__ int red_r[kLeafThreads / 32];
   __shared__ int win_s;
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
   const int mp = n - d0;
   const int r0 = b * R;
   const int rcount = mp - r0 < R ? (mp - r0 > 0 ? mp - r0 : 0) : R;
+  const int nleft = d0 - pc0;
+  const int nout = nleft + (pc1 - d0 - w);
+  const int q = tid * G + b;
+  double* ocol = q < nout ? A + static_cast<long>(q < nleft ? pc0 + q : d0 + w + (q - nleft)) * lda : nullptr;
+  long sw_c = -1, sw_p = -1;   // pending interchange of this thread's outside column
+  double sw_xc = 0.0, sw_xp = 0.0;
   for (int c = 0; c < w; ++c)
     for (int lr = tid; lr < rcount; lr += blockDim.x) P[c * R + lr] = A[(d0 + r0 + lr) + static_cast<long>(d0 + c) * lda];
   __syncthreads();
 
   for (int c = 0; c < w; ++c) {
     const int par = c & 1;
+    if (sw_c >= 0) {
+      ocol[sw_c] = sw_xp;
+      ocol[sw_p] = sw_xc;
+      sw_c = -1;
+    }
     // (a) local candidate for column c over own rows with panel row >= c
     uint64_t bv = 0;
     int br = 0x7FFFFFFF;
@@ -119,9 +133,9 @@ __global__ void __launch_bounds__(kLeafThreads) getf2_leaf_kernel(double* A, lon
         br = r2;
       }
     }
-    if ((tid & 31) == 0) {
-      red_v[tid >> 5] = bv;
-      red_r[tid >> 5] = br;
+    if (lane == 0) {
+      red_v[warp] = bv;
+      red_r[warp] = br;
     }
     __syncthreads();
     if (tid == 0) {
@@ -143,37 +157,53 @@ __global__ void __launch_bounds__(kLeafThreads) getf2_leaf_kernel(double* A, lon
         for (int cc = tid; cc < w; cc += blockDim.x) diag_rows[par * kLeaf + cc] = P[cc * R + (c - r0)];
     }
     // (b) one barrier per column
-    if (!grid_sync(gb, G, limit, status)) return;
-    // (c) global pivot
-    if (tid == 0) {
+    if (!grid_sync(gb, static_cast<unsigned long long>(c + 1) * G, limit, status)) return;
+    // (c) global pivot: warp 0 scans the G candidates and fetches the pivot
+    // row, warp 1 fetches row c
+    if (warp == 0) {
+      const volatile uint64_t* cv = cand_val + par * G;
+      const volatile int* ci = cand_idx + par * G;
       uint64_t gv = 0;
-      int gr = 0x7FFFFFFF, gb_ = 0;
-      volatile uint64_t* cv = cand_val;
-      volatile int* ci = cand_idx;
-      for (int i = 0; i < G; ++i) {
-        const uint64_t v = cv[par * G + i];
-        const int r = ci[par * G + i];
-        if (r != 0x7FFFFFFF && better(v, r, gv, gr)) {
+      int gr = 0x7FFFFFFF, gbk = 0;
+      for (int i = lane; i < G; i += 32) {
+        const uint64_t v = cv[i];
+        const int r = ci[i];
+        if (better(v, r, gv, gr)) {
           gv = v;
           gr = r;
-          gb_ = i;
+          gbk = i;
         }
       }
-      win_s = gr;
-      red_r[0] = gb_;
-      if (b == 0) {
-        ipiv[d0 + c] = d0 + gr + 1;
-        if (gv == 0) atomicCAS(info, 0, d0 + c + 1);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t v2 = __shfl_xor_sync(0xFFFFFFFFu, gv, o);
+        const int r2 = __shfl_xor_sync(0xFFFFFFFFu, gr, o);
+        const int b2 = __shfl_xor_sync(0xFFFFFFFFu, gbk, o);
+        if (better(v2, r2, gv, gr)) {
+          gv = v2;
+          gr = r2;
+          gbk = b2;
+        }
       }
+      if (lane < w) prow[lane] = static_cast<const volatile double*>(cand_rows)[(static_cast<long>(par) * G + gbk) * kLeaf + lane];
+      if (lane == 0) {
+        win_s = gr;
+        if (b == 0) {
+          ipiv[d0 + c] = d0 + gr + 1;
+          if (gv == 0) atomicCAS(info, 0, d0 + c + 1);
+        }
+      }
+    } else if (warp == 1) {
+      if (lane < w) crow[lane] = static_cast<const volatile double*>(diag_rows)[par * kLeaf + lane];
     }
     __syncthreads();
     const int p = win_s;
-    const int pb = red_r[0];
-    for (int cc = tid; cc < w; cc += blockDim.x) {
-      prow[cc] = static_cast<volatile double*>(cand_rows)[(static_cast<long>(par) * G + pb) * kLeaf + cc];
-      crow[cc] = static_cast<volatile double*>(diag_rows)[par * kLeaf + cc];
+    if (ocol && p != c) {
+      sw_c = d0 + c;
+      sw_p = d0 + p;
+      sw_xc = ocol[sw_c];
+      sw_xp = ocol[sw_p];
     }
-    __syncthreads();
     const double piv = prow[c];
     if (piv != 0.0) {
       if (p != c) {
@@ -195,6 +225,10 @@ __global__ void __launch_bounds__(kLeafThreads) getf2_leaf_kernel(double* A, lon
     }
     __syncthreads();
   }
+  if (sw_c >= 0) {
+    ocol[sw_c] = sw_xp;
+    ocol[sw_p] = sw_xc;
+  }
   for (int c = 0; c < w; ++c)
     for (int lr = tid; lr < rcount; lr += blockDim.x) A[(d0 + r0 + lr) + static_cast<long>(d0 + c) * lda] = P[c * R + lr];
 }
@@ -210,10 +244,15 @@ __global__ void laswp_perm_kernel(const int32_t* ipiv, int k1, int k2, int* map 
   __shared__ int cont[kPermMax];                 // content of rows k1..k2-1
   __shared__ int hkey[kHash], hval[kHash];       // rows >= k2 that were touched
   __shared__ int order[kPermMax];
-  if (threadIdx.x != 0) return;
+  __shared__ int piv_s[kPermMax];
   const int nb = k2 - k1;
-  for (int i = 0; i < nb; ++i) cont[i] = k1 + i;
-  for (int i = 0; i < kHash; ++i) hkey[i] = -1;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    cont[i] = k1 + i;
+    piv_s[i] = ipiv[k1 + i] - 1;
+  }
+  for (int i = threadIdx.x; i < kHash; i += blockDim.x) hkey[i] = -1;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   int nout = 0;
   auto slot_of = [&](int row) {
     int h = (row * 2654435761u) & (kHash - 1);
@@ -221,7 +260,7 @@ __global__ void laswp_perm_kernel(const int32_t* ipiv, int k1, int k2, int* map 
     return h;
   };
   for (int k = k1; k < k2; ++k) {
-    const int p = ipiv[k] - 1;
+    const int p = piv_s[k - k1];
     if (p == k) continue;
     if (p < k2) {
       const int t = cont[k - k1];
@@ -283,18 +322,41 @@ __global__ void __launch_bounds__(256) laswp_apply_kernel(double* A, long lda, i
   }
 }
 
-// X (w1 x w2 at A[d0.., c0..]) <- L^-1 X with L unit lower w1 x w1 at A[d0.., d0..].
-__global__ void trsm_small_kernel(double* A, long lda, int d0, int w1, int c0) {
-  __shared__ double x[128];
-  const int j = c0 + blockIdx.x, i = threadIdx.x;
-  double* col = A + static_cast<long>(j) * lda + d0;
-  if (i < w1) x[i] = col[i];
-  __syncthreads();
-  for (int k = 0; k < w1; ++k) {
-    if (i > k && i < w1) x[i] = fma(-A[(d0 + i) + static_cast<long>(d0 + k) * lda], x[k], x[i]);
-    __syncthreads();
+// X (w1 x w2 at A[d0.., c0..]) <- L^-1 X with L unit lower w1 x w1 at A[d0.., d0..]
+// (w1 <= 128).  The strictly lower part of L is staged in shared memory; one
+// warp per column of X, lane l holding rows l, l+32, l+64, l+96 in registers,
+// x_k broadcast by shuffle.
+constexpr int kTrsmMax = 128;
+__global__ void __launch_bounds__(256) trsm_small_kernel(double* A, long lda, int d0, int w1, int c0, int w2) {
+  extern __shared__ double Ls[];   // Ls[i + k*w1] = L(i, k) for i > k, else 0
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int e = tid; e < w1 * w1; e += blockDim.x) {
+    const int i = e % w1, k = e / w1;
+    Ls[e] = i > k ? A[(d0 + i) + static_cast<long>(d0 + k) * lda] : 0.0;
   }
-  if (i < w1) col[i] = x[i];
+  __syncthreads();
+  const int j = blockIdx.x * (blockDim.x / 32) + (tid >> 5);
+  if (j >= w2) return;
+  double* col = A + static_cast<long>(c0 + j) * lda + d0;
+  double x[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) x[t] = lane + 32 * t < w1 ? col[lane + 32 * t] : 0.0;
+#pragma unroll
+  for (int t0 = 0; t0 < 4; ++t0) {
+    for (int kk = 0; kk < 32; ++kk) {
+      const int k = 32 * t0 + kk;
+      if (k >= w1) break;
+      const double xk = __shfl_sync(0xFFFFFFFFu, x[t0], kk);
+#pragma unroll
+      for (int t = t0; t < 4; ++t) {
+        const int i = lane + 32 * t;
+        if (i > k && i < w1) x[t] = fma(-Ls[i + k * w1], xk, x[t]);
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+    if (lane + 32 * t < w1) col[lane + 32 * t] = x[t];
 }
 
 // inv (nb x nb, ld nb) <- L^-1 for L = the nb x nb lower triangle at A[d0.., d0..]
@@ -585,8 +647,8 @@ LuBufs carve(emul_handle_t h, size_t off, int nb) {
   return b;
 }
 
-int launch_leaf(emul_handle_t h, double* A, long lda, int n, int d0, int w, int32_t* ipiv, int32_t* info,
-                const LuBufs& B) {
+int launch_leaf(emul_handle_t h, double* A, long lda, int n, int d0, int w, int pc0, int pc1, int32_t* ipiv,
+                int32_t* info, const LuBufs& B) {
   const int mp = n - d0;
   int G = (mp + 255) / 256;
   const int smem_rows_cap = 200 * 1024 / (w * 8);
@@ -605,7 +667,7 @@ int launch_leaf(emul_handle_t h, double* A, long lda, int n, int d0, int w, int3
   }
   long long limit = h->wait_limit;
   int* status = h->d_status;
-  void* args[] = {&A, const_cast<long*>(&lda), &n, &d0, &w, const_cast<int*>(&R), &ipiv, &info,
+  void* args[] = {&A, const_cast<long*>(&lda), &n, &d0, &w, const_cast<int*>(&R), &pc0, &pc1, &ipiv, &info,
                   const_cast<GridBar**>(&B.bar), const_cast<double**>(&B.cand_rows), const_cast<uint64_t**>(&B.cand_val),
                   const_cast<int**>(&B.cand_idx), const_cast<double**>(&B.diag_rows), &status, &limit};
   h->launches++;
@@ -639,20 +701,30 @@ int laswp(emul_handle_t h, double* A, long lda, int c0, int c1, const int32_t* i
   return laswp_apply(h, A, lda, c0, c1, map);
 }
 
-// Recursive panel factorization of rows d0..n-1, columns d0..d0+w-1.
-int rgetrf(emul_handle_t h, double* A, long lda, int n, int d0, int w, int32_t* ipiv, int32_t* info, int s,
-           const LuBufs& B, int depth = 1) {
-  if (w <= kLeaf) return launch_leaf(h, A, lda, n, d0, w, ipiv, info, B);
-  int* map = B.map + depth * kMapInts;
+int trsm_small(emul_handle_t h, double* A, long lda, int d0, int w1, int c0, int w2) {
+  if (w1 <= 0 || w2 <= 0) return EMUL_OK;
+  if (w1 > kTrsmMax) return set_error(h, EMUL_NOT_SUPPORTED, "panel trsm wider than 128");
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(trsm_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmMax * kTrsmMax * 8);
+    attr_set = true;
+  }
+  trsm_small_kernel<<<(w2 + 7) / 8, 256, static_cast<size_t>(w1) * w1 * 8, h->stream>>>(A, lda, d0, w1, c0, w2);
+  h->launches++;
+  return check_cuda(h, cudaGetLastError(), "panel trsm");
+}
+
+// Recursive panel factorization of rows d0..n-1, columns d0..d0+w-1, inside
+// the panel [pc0, pc1).  The leaves apply each interchange to all columns of
+// that panel, so the recursion itself swaps nothing.
+int rgetrf(emul_handle_t h, double* A, long lda, int n, int d0, int w, int pc0, int pc1, int32_t* ipiv,
+           int32_t* info, int s, const LuBufs& B) {
+  if (w <= kLeaf) return launch_leaf(h, A, lda, n, d0, w, pc0, pc1, ipiv, info, B);
   const int w1 = (w / 2 + 7) / 8 * 8;
   const int w2 = w - w1;
-  int rc = rgetrf(h, A, lda, n, d0, w1, ipiv, info, s, B, depth + 1);
+  int rc = rgetrf(h, A, lda, n, d0, w1, pc0, pc1, ipiv, info, s, B);
   if (rc) return rc;
-  rc = laswp(h, A, lda, d0 + w1, d0 + w, ipiv, d0, d0 + w1, map);
-  if (rc) return rc;
-  trsm_small_kernel<<<w2, 128, 0, h->stream>>>(A, lda, d0, w1, d0 + w1);
-  h->launches++;
-  rc = check_cuda(h, cudaGetLastError(), "panel trsm");
+  rc = trsm_small(h, A, lda, d0, w1, d0 + w1, w2);
   if (rc) return rc;
   const int m2 = n - d0 - w1;
   // A22 (m2 x w2) -= A21 (m2 x w1) * A12 (w1 x w2)
@@ -660,9 +732,7 @@ int rgetrf(emul_handle_t h, double* A, long lda, int n, int d0, int w, int32_t* 
                 Operand{A + d0 + static_cast<long>(d0 + w1) * lda, lda, 1}, 1.0,
                 A + (d0 + w1) + static_cast<long>(d0 + w1) * lda, lda, s, false, 0, nullptr, 0, 0);
   if (rc) return rc;
-  rc = rgetrf(h, A, lda, n, d0 + w1, w2, ipiv, info, s, B, depth + 1);
-  if (rc) return rc;
-  return laswp(h, A, lda, d0, d0 + w1, ipiv, d0 + w1, d0 + w, map);
+  return rgetrf(h, A, lda, n, d0 + w1, w2, pc0, pc1, ipiv, info, s, B);
 }
 
 }  // namespace
@@ -705,7 +775,7 @@ int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int n
   const emul::LuBufs B = emul::carve(h, gw, nb);
   for (int j0 = 0; j0 < n; j0 += nb) {
     const int jb = nb < n - j0 ? nb : n - j0;
-    rc = emul::rgetrf(h, A, lda, n, j0, jb, ipiv, info, autos ? s_prev : s_fixed, B);
+    rc = emul::rgetrf(h, A, lda, n, j0, jb, j0, j0 + jb, ipiv, info, autos ? s_prev : s_fixed, B);
     if (rc) return rc;
     rc = emul::laswp_prepare(h, ipiv, j0, j0 + jb, B.map);
     if (rc) return rc;
