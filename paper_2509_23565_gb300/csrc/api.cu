@@ -40,18 +40,114 @@ int pairs_at(int s, int L) {
   return n;
 }
 
-// Build the sweep schedule.  Jobs: a level L whose n_L slice pairs fit the
-// exactness budget over the whole K (n_L * K <= 1040) is one job; otherwise
-// (narrow variant) its pairs are split into groups that fit, or (wide variant)
-// its K range is split into segments.  Levels are consumed in ascending order;
-// consecutive jobs of one K range are paired into sweeps.  In the narrow
-// variant the last level's jobs (at most two) form a final held sweep.
-bool build_schedule(int s, int nch, bool wide, std::vector<Sweep>& out) {
+// Highest slice index in a pair of level L.
+int level_planes(int s, int L) { return L - 1 < s ? L - 1 : s; }
+
+// K chunks per accumulator job of n slice pairs under the exactness budget.
+int seg_chunks(int n) { return n > 0 ? kExactBudget / (n * kBK) : 0; }
+
+struct Job {
+  int L, pb, pe, c0, c1, flags, rel;
+};
+
+Job make_job(int s, int L, int c0, int c1, int flags, int rel) {
+  const int pb = L - s > 1 ? L - s : 1;
+  const int pe = L - 1 < s ? L - 1 : s;
+  return Job{L, pb, pe, c0, c1, flags, rel};
+}
+
+void push_sweep(std::vector<Sweep>& out, const Job& a, const Job* b) {
+  Sweep sw{};
+  sw.k0c = static_cast<int16_t>(a.c0);
+  sw.k1c = static_cast<int16_t>(a.c1);
+  const Job* js[2] = {&a, b};
+  int np = 0;
+  for (int j = 0; j < 2 && js[j]; ++j) {
+    sw.L[j] = static_cast<int8_t>(js[j]->L);
+    sw.pb[j] = static_cast<int8_t>(js[j]->pb);
+    sw.pe[j] = static_cast<int8_t>(js[j]->pe);
+    sw.flags[j] = static_cast<int8_t>(js[j]->flags);
+    sw.rel[j] = static_cast<int8_t>(js[j]->rel);
+    const int pj = js[j]->pe > js[j]->L - js[j]->pb ? js[j]->pe : js[j]->L - js[j]->pb;
+    np = np > pj ? np : pj;
+  }
+  sw.nplanes = static_cast<int8_t>(np);
+  out.push_back(sw);
+}
+
+// Banded schedule: the levels are covered by bands of one level or of two
+// adjacent levels.  A two-level band (L, L+1) shares every staged chunk
+// between both levels (the planes of L are a subset of those of L+1); when
+// the pair does not fit the exactness budget over the whole K it runs as two
+// K halves, the first half of L+1 stashed until L is complete.  The bands
+// minimise the staged planes per K chunk (dynamic programme over the levels).
+bool build_banded(int s, int nch, bool wide, std::vector<Sweep>& out) {
   out.clear();
   const int t = s + 1;
-  struct Job {
-    int L, pb, pe, c0, c1;
-  };
+  const int kInf = 1 << 28;
+  std::vector<int> cost(t + 3, 0), choice(t + 3, 0);
+  auto groups = [&](int seg) { return (nch + seg - 1) / seg; };
+  for (int L = t; L >= 2; --L) {
+    cost[L] = kInf;
+    const int sg1 = seg_chunks(pairs_at(s, L));
+    if (sg1 >= 1 && cost[L + 1] < kInf && (wide || L < t || groups(sg1) <= 2)) {
+      cost[L] = level_planes(s, L) + cost[L + 1];
+      choice[L] = 1;
+    }
+    if (L + 1 <= t && cost[L + 2] < kInf) {
+      const int a = seg_chunks(pairs_at(s, L)), b = seg_chunks(pairs_at(s, L + 1));
+      const int sg2 = a < b ? a : b;
+      if (sg2 >= 1 && groups(sg2) <= 2 && level_planes(s, L + 1) + cost[L + 2] < cost[L]) {
+        cost[L] = level_planes(s, L + 1) + cost[L + 2];
+        choice[L] = 2;
+      }
+    }
+  }
+  if (cost[2] >= kInf) return false;
+  for (int L = 2; L <= t;) {
+    if (choice[L] == 1) {
+      const int G = groups(seg_chunks(pairs_at(s, L)));
+      const int size = (nch + G - 1) / G;
+      const bool fin = !wide && L == t;
+      for (int g = 0; g < G; ++g) {
+        const int c0 = g * size, c1 = c0 + size < nch ? c0 + size : nch;
+        int flags = g == 0 ? kOpen : 0, rel = 0;
+        if (fin) {
+          if (G == 1) flags = kFinal;
+          else if (g == 0) flags = kStash, rel = 1;
+          else flags = kTake | kFinal;
+        }
+        push_sweep(out, make_job(s, L, c0, c1, flags, rel), nullptr);
+      }
+      L += 1;
+    } else {
+      const int a = seg_chunks(pairs_at(s, L)), b = seg_chunks(pairs_at(s, L + 1));
+      const int G = groups(a < b ? a : b);
+      const bool fin = !wide && L + 1 == t;
+      if (G == 1) {
+        const Job j1 = make_job(s, L + 1, 0, nch, fin ? kFinal : kOpen, 0);
+        push_sweep(out, make_job(s, L, 0, nch, kOpen, 0), &j1);
+      } else {
+        const int h = (nch + 1) / 2;
+        const Job j1 = make_job(s, L + 1, 0, h, kStash, 2);
+        push_sweep(out, make_job(s, L, 0, h, kOpen, 0), &j1);
+        const Job j2 = make_job(s, L + 1, h, nch, kTake | (fin ? kFinal : kOpen), 0);
+        push_sweep(out, make_job(s, L, h, nch, 0, 0), &j2);
+      }
+      L += 2;
+    }
+  }
+  return true;
+}
+
+// Level-ordered schedule: a level whose n_L pairs fit the budget over the whole
+// K is one job; otherwise (narrow variant) its pairs are split into groups that
+// fit, or (wide variant) its K range into segments.  Consecutive jobs of one K
+// range share a sweep.  In the narrow variant the last level's jobs (at most
+// two) form the final sweep.
+bool build_levelwise(int s, int nch, bool wide, std::vector<Sweep>& out) {
+  out.clear();
+  const int t = s + 1;
   std::vector<Job> jobs, held;
   const int kc = nch * kBK;
   for (int L = 2; L <= t; ++L) {
@@ -60,55 +156,101 @@ bool build_schedule(int s, int nch, bool wide, std::vector<Sweep>& out) {
     const int n = pe - pb + 1;
     std::vector<Job>& dst = (!wide && L == t) ? held : jobs;
     if (n * kc <= kExactBudget) {
-      dst.push_back(Job{L, pb, pe, 0, nch});
+      dst.push_back(Job{L, pb, pe, 0, nch, kOpen, 0});
     } else if (!wide) {
       const int per = kExactBudget / kc;          // pairs per job
       if (per < 1) return false;
-      for (int p = pb; p <= pe; p += per) dst.push_back(Job{L, p, p + per - 1 < pe ? p + per - 1 : pe, 0, nch});
+      for (int p = pb; p <= pe; p += per)
+        dst.push_back(Job{L, p, p + per - 1 < pe ? p + per - 1 : pe, 0, nch, p == pb ? kOpen : 0, 0});
     } else {
       int cm = kExactBudget / (kBK * n);
       if (cm < 1) cm = 1;
-      for (int c0 = 0; c0 < nch; c0 += cm) dst.push_back(Job{L, pb, pe, c0, c0 + cm < nch ? c0 + cm : nch});
+      for (int c0 = 0; c0 < nch; c0 += cm)
+        dst.push_back(Job{L, pb, pe, c0, c0 + cm < nch ? c0 + cm : nch, c0 == 0 ? kOpen : 0, 0});
     }
   }
   if (held.size() > 2) return false;
-  auto planes_of = [&](const Job& j) { return j.pe > j.L - j.pb ? j.pe : j.L - j.pb; };
   for (size_t i = 0; i < jobs.size();) {
-    Sweep sw{};
-    sw.k0c = static_cast<int16_t>(jobs[i].c0);
-    sw.k1c = static_cast<int16_t>(jobs[i].c1);
-    sw.L[0] = static_cast<int8_t>(jobs[i].L);
-    sw.pb[0] = static_cast<int8_t>(jobs[i].pb);
-    sw.pe[0] = static_cast<int8_t>(jobs[i].pe);
-    int np = planes_of(jobs[i]);
-    size_t used = 1;
     if (i + 1 < jobs.size() && jobs[i + 1].c0 == jobs[i].c0 && jobs[i + 1].c1 == jobs[i].c1) {
-      sw.L[1] = static_cast<int8_t>(jobs[i + 1].L);
-      sw.pb[1] = static_cast<int8_t>(jobs[i + 1].pb);
-      sw.pe[1] = static_cast<int8_t>(jobs[i + 1].pe);
-      np = np > planes_of(jobs[i + 1]) ? np : planes_of(jobs[i + 1]);
-      used = 2;
+      push_sweep(out, jobs[i], &jobs[i + 1]);
+      i += 2;
+    } else {
+      push_sweep(out, jobs[i], nullptr);
+      i += 1;
     }
-    sw.nplanes = static_cast<int8_t>(np);
-    out.push_back(sw);
-    i += used;
   }
-  if (!held.empty()) {
-    Sweep sw{};
-    sw.k0c = 0;
-    sw.k1c = static_cast<int16_t>(nch);
-    sw.held = 1;
-    int np = 0;
-    for (size_t j = 0; j < held.size(); ++j) {
-      sw.L[j] = static_cast<int8_t>(held[j].L);
-      sw.pb[j] = static_cast<int8_t>(held[j].pb);
-      sw.pe[j] = static_cast<int8_t>(held[j].pe);
-      np = np > planes_of(held[j]) ? np : planes_of(held[j]);
-    }
-    sw.nplanes = static_cast<int8_t>(np);
-    out.push_back(sw);
+  if (held.size() == 1) {
+    held[0].flags = kFinal;
+    push_sweep(out, held[0], nullptr);
+  } else if (held.size() == 2) {
+    held[0].flags = kStash;
+    held[0].rel = 1;
+    held[1].flags = kTake | kFinal;
+    push_sweep(out, held[0], &held[1]);
   }
   return true;
+}
+
+// TMEM slot of every job.  The MMA issuer and the epilogue follow one rule:
+// a job takes the slot whose current job is released earliest in drain order
+// (ties: lowest slot); a stashed job is released with its kTake partner, any
+// other job when it is drained (in level-sum mode, mode 1, every job is
+// drained at once).  The rule is simulated tile by tile until the slot state
+// (release points relative to the tile, use-count parities) repeats; the
+// table holds the transient tiles and one period.  A sweep may only take
+// slots released by jobs before it, otherwise the schedule is rejected.
+bool plan_slots(const std::vector<Sweep>& sw, bool mode1, std::vector<uint8_t>& tab, int& njobs, int& t0,
+                int& period) {
+  std::vector<int> first_of_job, relo;
+  for (const Sweep& w : sw) {
+    const int first = static_cast<int>(relo.size());
+    for (int j = 0; j < 2 && w.L[j]; ++j) {
+      first_of_job.push_back(first);
+      relo.push_back(!mode1 && (w.flags[j] & kStash) ? w.rel[j] : 0);
+    }
+  }
+  njobs = static_cast<int>(relo.size());
+  if (njobs == 0) return false;
+  constexpr int kS = 4, kMaxTiles = 64;
+  constexpr long long kFree = -(1ll << 40);
+  long long rel[kS];
+  int cnt[kS];
+  for (int i = 0; i < kS; ++i) rel[i] = kFree, cnt[i] = 0;
+  std::vector<std::vector<long long>> states;
+  tab.clear();
+  for (int tile = 0; tile < kMaxTiles; ++tile) {
+    const long long base = static_cast<long long>(tile) * njobs;
+    std::vector<long long> key;
+    for (int i = 0; i < kS; ++i) {
+      key.push_back(rel[i] == kFree ? kFree : rel[i] - base);
+      key.push_back(cnt[i] & 1);
+    }
+    for (size_t i0 = 0; i0 < states.size(); ++i0)
+      if (states[i0] == key) {
+        t0 = static_cast<int>(i0);
+        period = tile - t0;
+        return true;
+      }
+    states.push_back(key);
+    for (int j = 0; j < njobs; ++j) {
+      int b = 0;
+      for (int i = 1; i < kS; ++i)
+        if (rel[i] < rel[b]) b = i;
+      if (rel[b] >= base + first_of_job[j]) return false;
+      tab.push_back(static_cast<uint8_t>(b | ((cnt[b] & 1) << 2)));
+      rel[b] = base + j + relo[j];
+      cnt[b]++;
+    }
+  }
+  return false;
+}
+
+// Schedule and slot plan: the banded schedule when it exists and plans, else
+// the level-ordered one.
+bool build_schedule(int s, int nch, bool wide, bool mode1, std::vector<Sweep>& out, std::vector<uint8_t>& tab,
+                    int& njobs, int& t0, int& period) {
+  if (build_banded(s, nch, wide, out) && plan_slots(out, mode1, tab, njobs, t0, period)) return true;
+  return build_levelwise(s, nch, wide, out) && plan_slots(out, mode1, tab, njobs, t0, period);
 }
 
 // The narrow variant keeps the Horner state in int64 and rounds T = R 2^7 + I
@@ -118,29 +260,44 @@ bool narrow_ok(int s, int k) {
   if (s > 7) return false;
   const int nch = (k + kBK - 1) / kBK;
   std::vector<Sweep> tmp;
-  if (!build_schedule(s, nch, false, tmp)) return false;
+  std::vector<uint8_t> tab;
+  int nj, t0, per;
+  if (!build_schedule(s, nch, false, false, tmp, tab, nj, t0, per)) return false;
   const long double bound = horner_bound_per_k(s) * static_cast<long double>(nch * kBK);
   return bound < 4.0e18L;   // < 2^62
 }
 
-int get_schedule(emul_handle_t h, int s, int nch, bool wide, Sweep** dptr, int* count) {
-  const uint32_t key = (static_cast<uint32_t>(s) << 24) | (static_cast<uint32_t>(wide) << 23) | static_cast<uint32_t>(nch);
+// Device copy of a schedule: the sweeps, then the slot table (16-byte aligned).
+size_t schedule_bytes(size_t nsweeps, size_t ntab) { return nsweeps * sizeof(Sweep) + 16 + ntab; }
+
+int get_schedule(emul_handle_t h, int s, int nch, bool wide, bool mode1, Sweep** dptr, int* count, SlotPlan* plan) {
+  const uint32_t key = (static_cast<uint32_t>(s) << 24) | (static_cast<uint32_t>(wide) << 23) |
+                       (static_cast<uint32_t>(mode1) << 22) | static_cast<uint32_t>(nch);
   auto it = h->sched_cache.find(key);
   if (it != h->sched_cache.end()) {
-    *dptr = it->second.first;
-    *count = it->second.second;
+    *dptr = it->second.sched;
+    *count = it->second.nsweeps;
+    *plan = it->second.plan;
     return EMUL_OK;
   }
   std::vector<Sweep> v;
-  if (!build_schedule(s, nch, wide, v)) return set_error(h, EMUL_INVALID_ARG, "no schedule for this slice count / k");
-  Sweep* d = nullptr;
-  if (cudaMalloc(&d, v.size() * sizeof(Sweep)) != cudaSuccess)
-    return set_error(h, EMUL_NO_WORKSPACE, "schedule allocation failed");
-  if (cudaMemcpy(d, v.data(), v.size() * sizeof(Sweep), cudaMemcpyHostToDevice) != cudaSuccess)
+  std::vector<uint8_t> tab;
+  SlotPlan sp{};
+  if (!build_schedule(s, nch, wide, mode1, v, tab, sp.njobs, sp.t0, sp.period))
+    return set_error(h, EMUL_INVALID_ARG, "no schedule for this slice count / k");
+  const size_t off_tab = (v.size() * sizeof(Sweep) + 15) / 16 * 16;
+  std::vector<uint8_t> blob(off_tab + tab.size(), 0);
+  std::memcpy(blob.data(), v.data(), v.size() * sizeof(Sweep));
+  std::memcpy(blob.data() + off_tab, tab.data(), tab.size());
+  uint8_t* d = nullptr;
+  if (cudaMalloc(&d, blob.size()) != cudaSuccess) return set_error(h, EMUL_NO_WORKSPACE, "schedule allocation failed");
+  if (cudaMemcpy(d, blob.data(), blob.size(), cudaMemcpyHostToDevice) != cudaSuccess)
     return set_error(h, EMUL_CUDA_ERROR, "schedule upload failed");
-  h->sched_cache[key] = {d, static_cast<int>(v.size())};
-  *dptr = d;
+  sp.tab = d + off_tab;
+  h->sched_cache[key] = emul_handle_s::SchedEntry{reinterpret_cast<Sweep*>(d), static_cast<int>(v.size()), sp};
+  *dptr = reinterpret_cast<Sweep*>(d);
   *count = static_cast<int>(v.size());
+  *plan = sp;
   return EMUL_OK;
 }
 
@@ -266,7 +423,8 @@ int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Oper
   const int nch = (k + kBK - 1) / kBK;
   Sweep* sched = nullptr;
   int nsweeps = 0;
-  rc = get_schedule(h, s, nch, wide, &sched, &nsweeps);
+  SlotPlan plan{};
+  rc = get_schedule(h, s, nch, wide, mode == 1, &sched, &nsweeps, &plan);
   if (rc) return rc;
   const int BN = wide ? 64 : 128;
   CUtensorMap tmA, tmB;
@@ -289,6 +447,7 @@ int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Oper
   a.fb = fb;
   a.sched = sched;
   a.nsweeps = nsweeps;
+  a.slots = plan;
   a.tiles_m = (m + 127) / 128;
   a.tiles_n = (n + BN - 1) / BN;
   a.lower = lower ? 1 : 0;
@@ -302,9 +461,9 @@ int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Oper
   a.wait_limit = h->wait_limit;
 
   const size_t stage = gemm_stage_bytes(wide, s);
-  const size_t budget = 232448 - 1024 - 512;
+  const size_t budget = 232448 - 1024 - 2048;
   int stages = static_cast<int>(budget / stage);
-  if (stages > 4) stages = 4;
+  if (stages > kMaxStagesCfg) stages = kMaxStagesCfg;
   if (stages < 2) return set_error(h, EMUL_NOT_SUPPORTED, "slice tiles do not fit in shared memory");
   const size_t smem = stages * stage + 1024;
   const int grid = a.ntiles < h->nsm ? a.ntiles : h->nsm;
@@ -372,7 +531,7 @@ int emul_create(emul_handle_t* handle, void* stream) {
 int emul_destroy(emul_handle_t h) {
   if (!h) return EMUL_INVALID_ARG;
   cudaStreamSynchronize(h->stream);
-  for (auto& kv : h->sched_cache) cudaFree(kv.second.first);
+  for (auto& kv : h->sched_cache) cudaFree(kv.second.sched);
   for (auto& r : h->recs) {
     cudaEventDestroy(r.e0);
     cudaEventDestroy(r.e1);
@@ -481,7 +640,7 @@ namespace emul {
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;   // 16 MiB
-constexpr size_t kNoAllocSchedBytes = 16384;                // room for 2048 sweeps
+constexpr size_t kNoAllocSchedBytes = 16384;                // sweeps (16 B each) and the slot table
 constexpr int kNoAllocMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
@@ -574,11 +733,18 @@ extern "C" int emul_dgemm_noalloc(void* stream, int m, int n, int k, double alph
   const bool wide = !narrow_ok(slices, k);
   const int nch = (k + kBK - 1) / kBK;
   std::vector<Sweep> v;
-  if (!build_schedule(slices, nch, wide, v)) return EMUL_INVALID_ARG;
-  if (v.size() * sizeof(Sweep) > kNoAllocSchedBytes) return EMUL_NO_WORKSPACE;
+  std::vector<uint8_t> tab;
+  SlotPlan plan{};
+  if (!build_schedule(slices, nch, wide, false, v, tab, plan.njobs, plan.t0, plan.period)) return EMUL_INVALID_ARG;
+  const size_t off_tab = (v.size() * sizeof(Sweep) + 15) / 16 * 16;
+  if (off_tab + tab.size() > kNoAllocSchedBytes) return EMUL_NO_WORKSPACE;
+  std::vector<uint8_t> blob(off_tab + tab.size(), 0);
+  std::memcpy(blob.data(), v.data(), v.size() * sizeof(Sweep));
+  std::memcpy(blob.data() + off_tab, tab.data(), tab.size());
+  plan.tab = reinterpret_cast<const uint8_t*>(sched) + off_tab;
   // the status word must start at zero; the rest is fully rewritten by this call
   if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return EMUL_CUDA_ERROR;
-  if (cudaMemcpyAsync(sched, v.data(), v.size() * sizeof(Sweep), cudaMemcpyHostToDevice, st) != cudaSuccess)
+  if (cudaMemcpyAsync(sched, blob.data(), blob.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
     return EMUL_CUDA_ERROR;
   if (launch_split(st, m, k, A, 1, lda, slices, ea, sa, kp) != cudaSuccess) return EMUL_CUDA_ERROR;
   if (launch_split(st, n, k, B, ldb, 1, slices, fb, sb, kp) != cudaSuccess) return EMUL_CUDA_ERROR;
@@ -602,14 +768,15 @@ extern "C" int emul_dgemm_noalloc(void* stream, int m, int n, int k, double alph
   a.fb = fb;
   a.sched = sched;
   a.nsweeps = static_cast<int>(v.size());
+  a.slots = plan;
   a.tiles_m = (m + 127) / 128;
   a.tiles_n = (n + BN - 1) / BN;
   a.ntiles = a.tiles_m * a.tiles_n;
   a.status = status;
   a.wait_limit = 2000000000LL;
   const size_t stage = gemm_stage_bytes(wide, slices);
-  int stages = static_cast<int>((232448 - 1024 - 512) / stage);
-  if (stages > 4) stages = 4;
+  int stages = static_cast<int>((232448 - 1024 - 2048) / stage);
+  if (stages > kMaxStagesCfg) stages = kMaxStagesCfg;
   if (stages < 2) return EMUL_NOT_SUPPORTED;
   const int grid = a.ntiles < d->nsm ? a.ntiles : d->nsm;
   return launch_gemm(st, wide, tmA, tmB, a, grid, stages, stages * stage + 1024) == cudaSuccess ? EMUL_OK

@@ -9,17 +9,36 @@ namespace emul {
 constexpr int kNonFinite = 2147483647;   // scale of a row / column holding Inf or NaN
 constexpr int kMaxSlices = 8;
 constexpr int kBK = 32;                  // K elements per staged chunk (64 B of BF16: SWIZZLE_64B)
+constexpr int kMaxStagesCfg = 8;         // deepest ring of staged chunks
 constexpr int kExactBudget = 1040;       // k * pairs per accumulator: 1040 * 127^2 < 2^24
 
 // One sweep of the product schedule: one or two accumulator jobs over the K
 // chunks [k0c, k1c), sharing the staged slice tiles of each chunk.  A job
 // sums the slice pairs (p, L-p), p = pb..pe, of one level L into one TMEM slot.
+// The epilogue takes the jobs in schedule order; flags say what it does with
+// each (Horner state R, level sum I of the job):
+//   kOpen   R <- R * 2^7 before the job is added (first job of a level);
+//   kStash  keep the slot untouched; the next kTake job adds its sum too and
+//           releases both slots (rel = jobs until that kTake job);
+//   kTake   add the stashed job's sum to this job's;
+//   kFinal  T = R * 2^7 + I is rounded and C updated (last job of the narrow variant).
+enum JobFlag : int8_t { kOpen = 1, kStash = 2, kTake = 4, kFinal = 8 };
 struct Sweep {
-  int16_t k0c, k1c;   // chunk range
-  int8_t L[2];        // job levels (L[1] = 0: one job)
-  int8_t pb[2], pe[2];// pair ranges
-  int8_t held;        // 1: the jobs are the last level, held for the final step
-  int8_t nplanes;     // slice planes 1..nplanes of A and of B are staged
+  int16_t k0c, k1c;    // chunk range
+  int8_t L[2];         // job levels (L[1] = 0: one job)
+  int8_t pb[2], pe[2]; // pair ranges
+  int8_t flags[2];     // JobFlag bits of the two jobs
+  int8_t rel[2];       // kStash: schedule distance to the kTake job
+  int8_t nplanes;      // slice planes 1..nplanes of A and of B are staged
+  int8_t pad;
+};
+
+// Slot assignment of the jobs: TMEM slot (bits 0-1) and the parity of the
+// slot's use count (bit 2) for job j of the tile-phase ph, at tab[ph * njobs + j];
+// the i-th tile of a CTA uses phase i (i < t0) or t0 + (i - t0) % period.
+struct SlotPlan {
+  const uint8_t* tab;
+  int njobs, t0, period;
 };
 
 struct GemmArgs {
@@ -32,6 +51,7 @@ struct GemmArgs {
   const int32_t* fb;        // column scales of B [N]
   const Sweep* sched;       // device array
   int nsweeps;
+  SlotPlan slots;           // TMEM slot of every job (device table)
   int tiles_m, tiles_n, ntiles;
   int lower;                // 1: only entries with row >= col are written
   int tri;                  // 1: tiles enumerated over the lower triangle (square tiles)

@@ -17,9 +17,11 @@
 // Warp roles (384 threads): warp 0 issues TMA loads of the slice tiles of each
 // K chunk into a ring of shared-memory stages; warp 1 owns TMEM (4 accumulator
 // slots) and issues the MMAs; warps 4-11 drain the slots and write C.  The
-// first warpgroup gives registers to the two epilogue warpgroups (setmaxnreg).  Sweeps
-// of one or two levels share the staged tiles of a chunk; two slots are filled
-// while the other two are drained.  All waits are bounded.
+// first warpgroup gives registers to the epilogue warpgroups (setmaxnreg).  A sweep
+// of one or two jobs shares the staged tiles of a chunk; each job's TMEM slot
+// (and the parity of its barriers) comes from a host-planned slot table, so the
+// issuer fills slots while the epilogue drains others, and a stashed job can
+// hold its slot until its partner is drained.  All waits are bounded.
 #include <cstdint>
 #include <type_traits>
 
@@ -37,8 +39,11 @@ constexpr int kLowRegs = 64;            // producer warpgroup after setmaxnreg.d
 constexpr int kHighRegs = 104;          // epilogue warpgroups: 128*64 + 512*104 = 61440
 constexpr int kSlots = 4;
 constexpr int kEpiWarps = 16;
-constexpr int kSchedSmem = 128;
-constexpr int kMaxStages = 4;
+constexpr int kSchedSmem = 64;
+constexpr int kTabSmem = 256;
+constexpr int kMaxStages = kMaxStagesCfg;
+constexpr uint32_t kRowBytes = kBK * 2;     // one K-major row of a staged tile
+constexpr uint32_t kSwizzleCode = kRowBytes == 64 ? 4u : 6u;   // descriptor code of SWIZZLE_64B / _32B
 constexpr int kStatusTimeout = -4;
 
 template <bool WIDE>
@@ -116,6 +121,12 @@ __device__ __forceinline__ void tile_coords(const GemmArgs& a, int tile, int& tm
 
 __device__ __forceinline__ bool aborted(volatile int* flag) { return *flag != 0; }
 
+// Slot-table row of the i-th tile of this CTA.
+__device__ __forceinline__ const uint8_t* slot_row(const uint8_t* tab, const SlotPlan& sp, long i) {
+  const long ph = i < sp.t0 ? i : sp.t0 + (i - sp.t0) % sp.period;
+  return tab + ph * sp.njobs;
+}
+
 __device__ __forceinline__ void raise_timeout(const GemmArgs& a, volatile int* flag) {
   atomicExch(a.status, kStatusTimeout);
   *flag = 1;
@@ -136,6 +147,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   __shared__ Sweep sched_s[kSchedSmem];   // the schedule, when it is short enough
+  __shared__ uint8_t tab_s[kTabSmem];     // the slot table, when it is short enough
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int s = a.s;
@@ -146,6 +158,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (sched_in_smem)
     for (int i = threadIdx.x; i < a.nsweeps; i += blockDim.x) sched_s[i] = a.sched[i];
   const Sweep* sched = sched_in_smem ? sched_s : a.sched;
+  const int ntab = (a.slots.t0 + a.slots.period) * a.slots.njobs;
+  const bool tab_in_smem = ntab <= kTabSmem;
+  if (tab_in_smem)
+    for (int i = threadIdx.x; i < ntab; i += blockDim.x) tab_s[i] = a.slots.tab[i];
+  const uint8_t* tab = tab_in_smem ? tab_s : a.slots.tab;
   if (threadIdx.x == 0) {
     for (int i = 0; i < stages; ++i) {
       mbar_init(&stage_full[i], 1);
@@ -207,18 +224,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16_f32(128, Cf::BN);
-      long it = 0, jc = 0;
+      long it = 0, tloc = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+      for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x, ++tloc) {
+        const uint8_t* srow = slot_row(tab, a.slots, tloc);
+        int jj = 0;
         for (int sw = 0; sw < a.nsweeps && ok; ++sw) {
           const Sweep S = sched[sw];
           const int nj = S.L[1] ? 2 : 1;
           uint32_t dcol[2];
+          int sl[2];
           for (int j = 0; j < nj; ++j) {
-            const long u = jc + j;
-            const int slot = (int)(u % kSlots);
+            const uint32_t e = srow[jj + j];
+            const int slot = (int)(e & 3u);
+            sl[j] = slot;
             dcol[j] = tmem + (uint32_t)(slot * Cf::BN);
-            if (aborted(abortp) || !mbar_wait(&slot_empty[slot], (uint32_t)((u / kSlots) & 1) ^ 1u, a.wait_limit)) {
+            if (aborted(abortp) || !mbar_wait(&slot_empty[slot], ((e >> 2) & 1u) ^ 1u, a.wait_limit)) {
               if (!aborted(abortp)) raise_timeout(a, abortp);
               ok = false;
               break;
@@ -246,15 +267,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int kk = 0; kk < kBK / 16; ++kk) {
                   const uint32_t acc = (kc != S.k0c || p != pb || kk != 0) ? 1u : 0u;
-                  mma_bf16(dcol[j], umma_desc(aa + kk * 32, 64, 4), umma_desc(ba + kk * 32, 64, 4), idesc, acc);
+                  mma_bf16(dcol[j], umma_desc(aa + kk * 32, kRowBytes, kSwizzleCode),
+                           umma_desc(ba + kk * 32, kRowBytes, kSwizzleCode), idesc, acc);
                 }
               }
             }
             mma_commit(&stage_empty[st]);
           }
           if (!ok) break;
-          for (int j = 0; j < nj; ++j) mma_commit(&slot_full[(jc + j) % kSlots]);
-          jc += nj;
+          for (int j = 0; j < nj; ++j) mma_commit(&slot_full[sl[j]]);
+          jj += nj;
         }
       }
       // every MMA issued by this thread must be complete before TMEM is released
@@ -274,9 +296,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const bool needs_c = (UPD == kSub) || (UPD == kGeneral && a.beta != 0.0);
     const int sh0 = -7 * a.t;
     State R[CPT];
-    long jc = 0;
+    long tloc = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+    for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x, ++tloc) {
       int tm, tn;
       tile_coords(a, tile, tm, tn);
       const int row = tm * Cf::BM + row_t;
@@ -296,113 +318,121 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
 #pragma unroll
       for (int c = 0; c < CPT; ++c) R[c] = 0;
-      int prevL = -1;
-      bool held_final = false;
+      const uint8_t* srow = slot_row(tab, a.slots, tloc);
+      int jj = 0;
+      int st_slot = 0;
+      uint32_t st_par = 0;
+      bool final_done = false;
       for (int sw = 0; sw < a.nsweeps && ok; ++sw) {
         const Sweep S = sched[sw];
         const int nj = S.L[1] ? 2 : 1;
-        if (S.held && a.mode == 0) {
-          // final step: T = R * 2^7 + (sum of the held jobs of the last level),
-          // rounded once, C updated in place
-          held_final = true;
-          int slots[2];
-          for (int j = 0; j < nj && ok; ++j) {
-            slots[j] = (int)((jc + j) % kSlots);
-            if (aborted(abortp) ||
-                !mbar_wait(&slot_full[slots[j]], (uint32_t)(((jc + j) / kSlots) & 1), a.wait_limit)) {
-              if (!aborted(abortp)) raise_timeout(a, abortp);
-              ok = false;
-            }
+        for (int j = 0; j < nj && ok; ++j, ++jj) {
+          const int fl = S.flags[j];
+          const uint32_t e = srow[jj];
+          const int slot = (int)(e & 3u);
+          const uint32_t par = (e >> 2) & 1u;
+          if (a.mode == 0 && (fl & kStash)) {
+            // left in its slot until the kTake job
+            st_slot = slot;
+            st_par = par;
+            continue;
           }
-          if (!ok) break;
-          tc_fence_after();
-          const uint32_t ta0 = tmem + lane_addr + (uint32_t)(slots[0] * Cf::BN + half * CPT);
-          const uint32_t ta1 = tmem + lane_addr + (uint32_t)(slots[nj - 1] * Cf::BN + half * CPT);
-          const bool rowok = row < a.M;
-#pragma unroll
-          for (int c4 = 0; c4 < CPT / 4; ++c4) {
-            uint32_t r0[4], r1[4];
-            tmem_ld4(ta0 + c4 * 4, r0);
-            tmem_ld4(ta1 + c4 * 4, r1);
-            double cv[4];
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-              const int col = col0 + c4 * 4 + jj;
-              cv[jj] = (needs_c && rowok && col < a.N) ? a.C[row + (long)col * a.ldc] : 0.0;
-            }
-            tmem_ld_wait();
-#pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-              const int c = c4 * 4 + jj;
-              const int col = col0 + c;
-              const int f = __shfl_sync(0xFFFFFFFFu, fcol[0], c);
-              if (!rowok || col >= a.N || (a.lower && row < col)) continue;
-              const int I = f2i(r0[jj]) + (nj == 2 ? f2i(r1[jj]) : 0);
-              double D;
-              if (e_row == kNonFinite || f == kNonFinite)
-                D = __longlong_as_double(0x7FF8000000000000ll);
-              else if (WIDE)
-                D = rn_scaled((__int128)R[c] * 128 + (__int128)I, e_row + f + sh0);
-              else
-                D = rn_split((long long)R[c], I, e_row + f + sh0);
-              a.C[row + (long)col * a.ldc] = apply_update<UPD>(a, D, cv[jj]);
-            }
-          }
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0)
-            for (int j = 0; j < nj; ++j) mbar_arrive(&slot_empty[slots[j]]);
-          jc += nj;
-          continue;
-        }
-        for (int j = 0; j < nj; ++j) {
-          const int L = S.L[j];
-          const int slot = (int)(jc % kSlots);
-          if (aborted(abortp) || !mbar_wait(&slot_full[slot], (uint32_t)((jc / kSlots) & 1), a.wait_limit)) {
+          const bool take = a.mode == 0 && (fl & kTake);
+          if (aborted(abortp) || !mbar_wait(&slot_full[slot], par, a.wait_limit) ||
+              (take && !mbar_wait(&slot_full[st_slot], st_par, a.wait_limit))) {
             if (!aborted(abortp)) raise_timeout(a, abortp);
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t taddr = tmem + lane_addr + (uint32_t)(slot * Cf::BN + half * CPT);
+          const uint32_t ta = tmem + lane_addr + (uint32_t)(slot * Cf::BN + half * CPT);
+          const uint32_t tb = tmem + lane_addr + (uint32_t)(st_slot * Cf::BN + half * CPT);
           if (a.mode == 1) {
             // level sums out (exact int32), added so that K segments / pair groups accumulate
+            const int L = S.L[j];
 #pragma unroll
             for (int c16 = 0; c16 < CPT / 16; ++c16) {
               uint32_t r[16];
-              tmem_ld16(taddr + c16 * 16, r);
+              tmem_ld16(ta + c16 * 16, r);
               tmem_ld_wait();
 #pragma unroll
-              for (int jj = 0; jj < 16; ++jj) {
-                const int col = col0 + c16 * 16 + jj;
+              for (int q = 0; q < 16; ++q) {
+                const int col = col0 + c16 * 16 + q;
                 if (row < a.M && col < a.N) {
                   int32_t* lp = a.levels + (long)(L - 2) * a.ldl_plane + row + (long)col * a.ldl;
-                  *lp += f2i(r[jj]);
+                  *lp += f2i(r[q]);
                 }
               }
             }
-          } else {
-            if (L != prevL) {
+          } else if (fl & kFinal) {
+            // final step: T = R * 2^7 + I (I of this job plus the stashed one),
+            // rounded once, C updated in place
+            final_done = true;
+            const bool rowok = row < a.M;
 #pragma unroll
-              for (int c = 0; c < CPT; ++c) R[c] = R[c] * (State)128;
-              prevL = L;
-            }
+            for (int c4 = 0; c4 < CPT / 4; ++c4) {
+              uint32_t r0[4], r1[4];
+              tmem_ld4(ta + c4 * 4, r0);
+              if (take) tmem_ld4(tb + c4 * 4, r1);
+              double cv[4];
 #pragma unroll
-            for (int c16 = 0; c16 < CPT / 16; ++c16) {
-              uint32_t r[16];
-              tmem_ld16(taddr + c16 * 16, r);
+              for (int q = 0; q < 4; ++q) {
+                const int col = col0 + c4 * 4 + q;
+                cv[q] = (needs_c && rowok && col < a.N) ? a.C[row + (long)col * a.ldc] : 0.0;
+              }
               tmem_ld_wait();
 #pragma unroll
-              for (int jj = 0; jj < 16; ++jj) R[c16 * 16 + jj] += (State)f2i(r[jj]);
+              for (int q = 0; q < 4; ++q) {
+                const int c = c4 * 4 + q;
+                const int col = col0 + c;
+                const int f = __shfl_sync(0xFFFFFFFFu, fcol[0], c);
+                if (!rowok || col >= a.N || (a.lower && row < col)) continue;
+                const int I = f2i(r0[q]) + (take ? f2i(r1[q]) : 0);
+                double D;
+                if (e_row == kNonFinite || f == kNonFinite)
+                  D = __longlong_as_double(0x7FF8000000000000ll);
+                else if (WIDE)
+                  D = rn_scaled((__int128)R[c] * 128 + (__int128)I, e_row + f + sh0);
+                else
+                  D = rn_split((long long)R[c], I, e_row + f + sh0);
+                a.C[row + (long)col * a.ldc] = apply_update<UPD>(a, D, cv[q]);
+              }
+            }
+          } else {
+            if (fl & kOpen) {
+#pragma unroll
+              for (int c = 0; c < CPT; ++c) R[c] = R[c] * (State)128;
+            }
+            if (!take) {
+#pragma unroll
+              for (int c16 = 0; c16 < CPT / 16; ++c16) {
+                uint32_t r[16];
+                tmem_ld16(ta + c16 * 16, r);
+                tmem_ld_wait();
+#pragma unroll
+                for (int q = 0; q < 16; ++q) R[c16 * 16 + q] += (State)f2i(r[q]);
+              }
+            } else {
+#pragma unroll
+              for (int c8 = 0; c8 < CPT / 8; ++c8) {
+                uint32_t r[8], r2[8];
+                tmem_ld8(ta + c8 * 8, r);
+                tmem_ld8(tb + c8 * 8, r2);
+                tmem_ld_wait();
+#pragma unroll
+                for (int q = 0; q < 8; ++q) R[c8 * 8 + q] += (State)(f2i(r[q]) + f2i(r2[q]));
+              }
             }
           }
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(&slot_empty[slot]);
-          ++jc;
+          if (lane == 0) {
+            mbar_arrive(&slot_empty[slot]);
+            if (take) mbar_arrive(&slot_empty[st_slot]);
+          }
         }
       }
-      if (ok && a.mode == 0 && !held_final) {
+      if (ok && a.mode == 0 && !final_done) {
         // every level was folded into R (wide variant): T = R
 #pragma unroll
         for (int c8 = 0; c8 < CPT / 8; ++c8) {

@@ -19,7 +19,12 @@ struct emul_handle_s {
   int* d_status = nullptr;          // device status word written by kernels
   void* ws = nullptr;               // workspace (device)
   size_t ws_bytes = 0;
-  std::map<uint32_t, std::pair<emul::Sweep*, int>> sched_cache;   // (s, chunks, wide) -> device schedule
+  struct SchedEntry {
+    emul::Sweep* sched;             // device: sweeps, then the slot table
+    int nsweeps;
+    emul::SlotPlan plan;
+  };
+  std::map<uint32_t, SchedEntry> sched_cache;   // (s, wide, level-sum mode, chunks) -> device schedule
   std::string last_error;
   void* encode_fn = nullptr;        // cuTensorMapEncodeTiled
   long long wait_limit = 2000000000LL;

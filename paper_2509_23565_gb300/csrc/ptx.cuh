@@ -105,7 +105,8 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // UMMA shared-memory descriptor, K-major operand with the given swizzle.
-//   swizzle: 2 = 128 B rows (atom 8 rows x 128 B), 4 = 64 B rows (atom 8 x 64 B)
+//   swizzle: 2 = 128 B rows (atom 8 rows x 128 B), 4 = 64 B rows (atom 8 x 64 B),
+//            6 = 32 B rows (atom 8 x 32 B)
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t row_bytes, uint32_t swizzle_code) {
   uint64_t d = 0;
   d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFF);
