@@ -31,36 +31,11 @@ constexpr int kStatusTimeout = -4;
 constexpr size_t kAl = 256;
 inline size_t al(size_t x) { return (x + kAl - 1) / kAl * kAl; }
 
+// Grid barrier of the cooperative leaf launch: a monotonic arrival counter,
+// zeroed before the launch; barrier number i completes when it reaches (i + 1) G.
 struct GridBar {
-  unsigned long long count;   // arrivals since the launch (zeroed before it)
+  unsigned long long count;
 };
-
-// Bounded grid-wide barrier for a cooperative launch of G blocks on a
-// monotonic arrival counter: barrier number i completes when the counter
-// reaches target = (i + 1) G, so no reset is needed between barriers.
-__device__ bool grid_sync(GridBar* gb, unsigned long long target, long long limit, int* status) {
-  __shared__ int ok_s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    bool ok = true;
-    if (atomicAdd(&gb->count, 1ull) + 1 < target) {
-      volatile unsigned long long* vc = &gb->count;
-      const long long t0 = clock64();
-      while (*vc < target) {
-        if (clock64() - t0 > limit) {
-          ok = false;
-          atomicExch(status, kStatusTimeout);
-          break;
-        }
-      }
-    }
-    __threadfence();
-    ok_s = ok;
-  }
-  __syncthreads();
-  return ok_s != 0;
-}
 
 __device__ __forceinline__ uint64_t absbits(double x) {
   return static_cast<uint64_t>(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFull;
@@ -74,22 +49,37 @@ __device__ __forceinline__ bool better(uint64_t v1, int r1, uint64_t v2, int r2)
 
 // Leaf panel: rows d0..n-1, columns d0..d0+w-1 of A, factored in place with
 // partial pivoting.  Block b keeps panel rows [b*R, b*R+R) in shared memory.
-// Every interchange is also applied to the columns [pc0, d0) and
-// [d0+w, pc1) of the enclosing panel, which live in global memory: the
-// outside column q (0-based over both ranges) belongs to thread q / G of block
-// q % G for the whole launch, so successive interchanges of one element stay
-// in program order.  Its loads are issued when the pivot is known and its
-// stores at the next column, off the critical path.
+//
+// Column c: (1) pivot search on column c over the block's rows, (2) the block's
+// candidate row and row c published, (3) arrival at the grid barrier, (4) while
+// the other blocks arrive, the rank-1 update of pivot c-1 on columns c+1..w-1,
+// (5) barrier wait, global pivot and pivot-row fetch, (6) row interchange,
+// (7) multipliers of column c and the update of column c+1 only, so that the
+// next pivot search can start.  Each entry receives the same FMAs in the same
+// order as in a plain right-looking elimination; the published rows get the
+// deferred update of pivot c-1 applied on the fly (the same FMA).
+//
+// Every interchange is also applied to the columns [pc0, d0) and [d0+w, pc1) of
+// the enclosing panel, which live in global memory: the outside column q
+// (0-based over both ranges) belongs to block q % G for the whole launch, to
+// the (q / G)-th of its threads other than thread 0 (it writes the block's
+// candidate) and the barrier lane (first lane of the last warp, which drives
+// the grid barrier and takes no part in the deferred update), so successive
+// interchanges of one element stay in program order.  Its loads are issued
+// when the pivot is known, its stores when the next pivot is known, off the
+// critical path.  At most 248 outside columns exist (panel <= 256 wide, leaf
+// >= 8 wide); 254 owners per block are available.
 __global__ void __launch_bounds__(kLeafThreads) getf2_leaf_kernel(double* A, long lda, int n, int d0, int w, int R,
                                                                  int pc0, int pc1, int32_t* ipiv, int32_t* info,
                                                                  GridBar* gb, double* cand_rows, uint64_t* cand_val,
                                                                  int* cand_idx, double* diag_rows, int* status,
                                                                  long long limit) {
   extern __shared__ double P[];   // P[c*R + lr]
-  __shared__ double prow[kLeaf], crow[kLeaf];
+  __shared__ double prow[2][kLeaf], crow[kLeaf];
+  __shared__ double rcp_s;
   __shared__ uint64_t red_v[kLeafThreads / 32];
   __shared__ int red_r[kLeafThreads / 32];
-  __shared__ int win_s;
+  __shared__ int win_s, ok_s;
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int mp = n - d0;
@@ -97,22 +87,21 @@ __global__ void __launch_bounds__(kLeafThreads) getf2_leaf_kernel(double* A, lon
   const int rcount = mp - r0 < R ? (mp - r0 > 0 ? mp - r0 : 0) : R;
   const int nleft = d0 - pc0;
   const int nout = nleft + (pc1 - d0 - w);
-  const int q = tid * G + b;
-  double* ocol = q < nout ? A + static_cast<long>(q < nleft ? pc0 + q : d0 + w + (q - nleft)) * lda : nullptr;
+  constexpr int kBarTid = kLeafThreads - 32;   // barrier lane
+  const int ot = (tid == 0 || tid == kBarTid) ? -1 : tid - 1 - (tid > kBarTid ? 1 : 0);
+  const int q = ot * G + b;
+  double* ocol = ot >= 0 && q < nout ? A + static_cast<long>(q < nleft ? pc0 + q : d0 + w + (q - nleft)) * lda : nullptr;
   long sw_c = -1, sw_p = -1;   // pending interchange of this thread's outside column
   double sw_xc = 0.0, sw_xp = 0.0;
+  bool pend = false;           // pivot c-1 was nonzero: its update of columns > c is pending
   for (int c = 0; c < w; ++c)
     for (int lr = tid; lr < rcount; lr += blockDim.x) P[c * R + lr] = A[(d0 + r0 + lr) + static_cast<long>(d0 + c) * lda];
   __syncthreads();
 
   for (int c = 0; c < w; ++c) {
     const int par = c & 1;
-    if (sw_c >= 0) {
-      ocol[sw_c] = sw_xp;
-      ocol[sw_p] = sw_xc;
-      sw_c = -1;
-    }
-    // (a) local candidate for column c over own rows with panel row >= c
+    const double* pv = prow[par ^ 1];   // pivot row of column c-1
+    // (1) local candidate for column c over own rows with panel row >= c
     uint64_t bv = 0;
     int br = 0x7FFFFFFF;
     for (int lr = tid; lr < rcount; lr += blockDim.x) {
@@ -149,17 +138,57 @@ __global__ void __launch_bounds__(kLeafThreads) getf2_leaf_kernel(double* A, lon
       win_s = br;
     }
     __syncthreads();
+    // (2) publish the candidate row and row c, current through pivot c-1
     {
       const int pr = win_s;
-      if (pr != 0x7FFFFFFF)
-        for (int cc = tid; cc < w; cc += blockDim.x) cand_rows[(static_cast<long>(par) * G + b) * kLeaf + cc] = P[cc * R + (pr - r0)];
-      if (c >= r0 && c < r0 + rcount)
-        for (int cc = tid; cc < w; cc += blockDim.x) diag_rows[par * kLeaf + cc] = P[cc * R + (c - r0)];
+      if (pr != 0x7FFFFFFF) {
+        const int lr = pr - r0;
+        for (int cc = tid; cc < w; cc += blockDim.x) {
+          double v = P[cc * R + lr];
+          if (pend && cc > c) v = fma(-P[(c - 1) * R + lr], pv[cc], v);
+          cand_rows[(static_cast<long>(par) * G + b) * kLeaf + cc] = v;
+        }
+      }
+      if (c >= r0 && c < r0 + rcount) {
+        const int lr = c - r0;
+        for (int cc = tid; cc < w; cc += blockDim.x) {
+          double v = P[cc * R + lr];
+          if (pend && cc > c) v = fma(-P[(c - 1) * R + lr], pv[cc], v);
+          diag_rows[par * kLeaf + cc] = v;
+        }
+      }
     }
-    // (b) one barrier per column
-    if (!grid_sync(gb, static_cast<unsigned long long>(c + 1) * G, limit, status)) return;
-    // (c) global pivot: warp 0 scans the G candidates and fetches the pivot
-    // row, warp 1 fetches row c
+    // (3) arrive (barrier lane), (4) deferred rank-1 update of pivot c-1 on
+    // columns c+1..w-1 (the other warps), (5) wait
+    __syncthreads();
+    if (tid == kBarTid) {
+      const unsigned long long target = static_cast<unsigned long long>(c + 1) * G;
+      __threadfence();
+      bool ok = true;
+      if (atomicAdd(&gb->count, 1ull) + 1 < target) {
+        volatile unsigned long long* vc = &gb->count;
+        const long long t0 = clock64();
+        while (*vc < target) {
+          if (clock64() - t0 > limit) {
+            ok = false;
+            atomicExch(status, kStatusTimeout);
+            break;
+          }
+        }
+      }
+      __threadfence();
+      ok_s = ok;
+    } else if (tid < kBarTid && pend && c + 1 < w) {
+      for (int lr = tid; lr < rcount; lr += kBarTid) {
+        if (r0 + lr <= c - 1) continue;
+        const double l = P[(c - 1) * R + lr];
+        for (int cc = c + 1; cc < w; ++cc) P[cc * R + lr] = fma(-l, pv[cc], P[cc * R + lr]);
+      }
+    }
+    __syncthreads();
+    if (!ok_s) return;
+    // global pivot: warp 0 scans the G candidates and fetches the pivot row,
+    // warp 1 fetches row c
     if (warp == 0) {
       const volatile uint64_t* cv = cand_val + par * G;
       const volatile int* ci = cand_idx + par * G;
@@ -185,7 +214,11 @@ __global__ void __launch_bounds__(kLeafThreads) getf2_leaf_kernel(double* A, lon
           gbk = b2;
         }
       }
-      if (lane < w) prow[lane] = static_cast<const volatile double*>(cand_rows)[(static_cast<long>(par) * G + gbk) * kLeaf + lane];
+      if (lane < w) {
+        const double pvv = static_cast<const volatile double*>(cand_rows)[(static_cast<long>(par) * G + gbk) * kLeaf + lane];
+        prow[par][lane] = pvv;
+        if (lane == c) rcp_s = 1.0 / pvv;
+      }
       if (lane == 0) {
         win_s = gr;
         if (b == 0) {
@@ -198,29 +231,39 @@ __global__ void __launch_bounds__(kLeafThreads) getf2_leaf_kernel(double* A, lon
     }
     __syncthreads();
     const int p = win_s;
-    if (ocol && p != c) {
-      sw_c = d0 + c;
-      sw_p = d0 + p;
-      sw_xc = ocol[sw_c];
-      sw_xp = ocol[sw_p];
+    if (ocol) {
+      if (sw_c >= 0) {
+        ocol[sw_c] = sw_xp;
+        ocol[sw_p] = sw_xc;
+        sw_c = -1;
+      }
+      if (p != c) {
+        sw_c = d0 + c;
+        sw_p = d0 + p;
+        sw_xc = ocol[sw_c];
+        sw_xp = ocol[sw_p];
+      }
     }
-    const double piv = prow[c];
-    if (piv != 0.0) {
+    const double piv = prow[par][c];
+    pend = piv != 0.0;
+    if (pend) {
+      // (6) interchange rows c and p (both current through pivot c-1)
       if (p != c) {
         if (c >= r0 && c < r0 + rcount)
-          for (int cc = tid; cc < w; cc += blockDim.x) P[cc * R + (c - r0)] = prow[cc];
+          for (int cc = tid; cc < w; cc += blockDim.x) P[cc * R + (c - r0)] = prow[par][cc];
         if (p >= r0 && p < r0 + rcount)
           for (int cc = tid; cc < w; cc += blockDim.x) P[cc * R + (p - r0)] = crow[cc];
       }
       __syncthreads();
+      // (7) multipliers of column c, update of column c+1
       const bool use_rcp = fabs(piv) >= 2.2250738585072014e-308;
-      const double rcp = 1.0 / piv;
+      const double rcp = rcp_s;
+      const double u1 = c + 1 < w ? prow[par][c + 1] : 0.0;
       for (int lr = tid; lr < rcount; lr += blockDim.x) {
-        const int pr = r0 + lr;
-        if (pr <= c) continue;
+        if (r0 + lr <= c) continue;
         const double l = use_rcp ? P[c * R + lr] * rcp : P[c * R + lr] / piv;
         P[c * R + lr] = l;
-        for (int cc = c + 1; cc < w; ++cc) P[cc * R + lr] = fma(-l, prow[cc], P[cc * R + lr]);
+        if (c + 1 < w) P[(c + 1) * R + lr] = fma(-l, u1, P[(c + 1) * R + lr]);
       }
     }
     __syncthreads();
