@@ -247,10 +247,25 @@ bool plan_slots(const std::vector<Sweep>& sw, bool mode1, std::vector<uint8_t>& 
 
 // Schedule and slot plan: the banded schedule when it exists and plans, else
 // the level-ordered one.
+// K chunks per stage: a stage holds s tiles of A and s of B, so a sweep that
+// stages fewer planes packs several chunks into one stage (one barrier phase
+// for more bytes; the copy engine's rate grows with the bytes per phase).
+void set_chunks_per_stage(int s, std::vector<Sweep>& out) {
+  for (Sweep& w : out) {
+    const int nc = w.k1c - w.k0c;
+    const int kmax = w.nplanes > 0 && s / w.nplanes > 1 ? s / w.nplanes : 1;
+    const int nst = (nc + kmax - 1) / kmax;
+    w.kcs = static_cast<int8_t>(nst > 0 ? (nc + nst - 1) / nst : 1);
+  }
+}
+
 bool build_schedule(int s, int nch, bool wide, bool mode1, std::vector<Sweep>& out, std::vector<uint8_t>& tab,
                     int& njobs, int& t0, int& period) {
-  if (build_banded(s, nch, wide, out) && plan_slots(out, mode1, tab, njobs, t0, period)) return true;
-  return build_levelwise(s, nch, wide, out) && plan_slots(out, mode1, tab, njobs, t0, period);
+  if (!(build_banded(s, nch, wide, out) && plan_slots(out, mode1, tab, njobs, t0, period)) &&
+      !(build_levelwise(s, nch, wide, out) && plan_slots(out, mode1, tab, njobs, t0, period)))
+    return false;
+  set_chunks_per_stage(s, out);
+  return true;
 }
 
 // The narrow variant keeps the Horner state in int64 and rounds T = R 2^7 + I

@@ -30,7 +30,7 @@ struct Sweep {
   int8_t flags[2];     // JobFlag bits of the two jobs
   int8_t rel[2];       // kStash: schedule distance to the kTake job
   int8_t nplanes;      // slice planes 1..nplanes of A and of B are staged
-  int8_t pad;
+  int8_t kcs;          // K chunks per stage (kcs * nplanes <= s tiles of A and of B)
 };
 
 // Slot assignment of the jobs: TMEM slot (bits 0-1) and the parity of the

@@ -14,9 +14,11 @@
 //   D = RN(T * 2^(e_i + f_j - 7t)),
 // and C = RN(RN(alpha D) + RN(beta C)) is written straight back.
 //
-// Warp roles (384 threads): warp 0 issues TMA loads of the slice tiles of each
+// Warp roles (640 threads): warp 0 issues TMA loads of the slice tiles of each
 // K chunk into a ring of shared-memory stages; warp 1 owns TMEM (4 accumulator
-// slots) and issues the MMAs; warps 4-11 drain the slots and write C.  The
+// slots); warps 1 and 2 issue the MMAs, one job of a sweep each (one issuing
+// thread cannot keep the tensor core busy with 128 x 128 x 16 MMAs); warps 4-19
+// drain the slots and write C.  The
 // first warpgroup gives registers to the epilogue warpgroups (setmaxnreg).  A sweep
 // of one or two jobs shares the staged tiles of a chunk; each job's TMEM slot
 // (and the parity of its barriers) comes from a host-planned slot table, so the
@@ -34,6 +36,7 @@ namespace emul {
 namespace {
 
 constexpr int kThreads = 640;          // 5 warpgroups: producer/MMA, 4 x epilogue
+constexpr int kMmaWarps = 2;            // warps 1 .. kMmaWarps issue MMAs
 constexpr int kLaunchRegs = 96;         // 640 x 96 = 61440 registers at launch
 constexpr int kLowRegs = 64;            // producer warpgroup after setmaxnreg.dec
 constexpr int kHighRegs = 104;          // epilogue warpgroups: 128*64 + 512*104 = 61440
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t stage_full[kMaxStages], stage_empty[kMaxStages];
-  __shared__ __align__(8) uint64_t slot_full[kSlots], slot_empty[kSlots], mma_done;
+  __shared__ __align__(8) uint64_t slot_full[kSlots], slot_empty[kSlots], mma_done[kMmaWarps];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   __shared__ Sweep sched_s[kSchedSmem];   // the schedule, when it is short enough
@@ -166,13 +169,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) {
     for (int i = 0; i < stages; ++i) {
       mbar_init(&stage_full[i], 1);
-      mbar_init(&stage_empty[i], 1);
+      mbar_init(&stage_empty[i], kMmaWarps);   // one commit per issuing warp
     }
     for (int i = 0; i < kSlots; ++i) {
       mbar_init(&slot_full[i], 1);
       mbar_init(&slot_empty[i], kEpiWarps);
     }
-    mbar_init(&mma_done, 1);
+    for (int i = 0; i < kMmaWarps; ++i) mbar_init(&mma_done[i], 1);
     abort_flag = 0;
     fence_mbar_init();
   }
@@ -197,7 +200,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int m0 = tm * Cf::BM, n0 = tn * Cf::BN;
         for (int sw = 0; sw < a.nsweeps && ok; ++sw) {
           const Sweep S = sched[sw];
-          for (int kc = S.k0c; kc < S.k1c; ++kc, ++it) {
+          const int np = S.nplanes;
+          for (int kc = S.k0c; kc < S.k1c; kc += S.kcs, ++it) {
+            const int nu = S.k1c - kc < S.kcs ? S.k1c - kc : S.kcs;
             const int st = (int)(it % stages);
             const uint32_t par = (uint32_t)((it / stages) & 1) ^ 1u;
             if (aborted(abortp) || !mbar_wait(&stage_empty[st], par, a.wait_limit)) {
@@ -206,11 +211,13 @@ __global__ void __launch_bounds__(kThreads, 1)
               break;
             }
             uint8_t* base = smem + (size_t)st * stage_bytes;
-            mbar_arrive_expect_tx(&stage_full[st], (uint32_t)S.nplanes * (Cf::A_TILE + Cf::B_TILE));
-            for (int p = 0; p < S.nplanes; ++p) {
-              tma_load_3d(base + p * Cf::A_TILE, &tmA, &stage_full[st], kc * kBK, m0, p);
-              tma_load_3d(base + s * Cf::A_TILE + p * Cf::B_TILE, &tmB, &stage_full[st], kc * kBK, n0, p);
-            }
+            mbar_arrive_expect_tx(&stage_full[st], (uint32_t)(nu * np) * (Cf::A_TILE + Cf::B_TILE));
+            for (int u = 0; u < nu; ++u)
+              for (int p = 0; p < np; ++p) {
+                const int t = u * np + p;
+                tma_load_3d(base + t * Cf::A_TILE, &tmA, &stage_full[st], (kc + u) * kBK, m0, p);
+                tma_load_3d(base + s * Cf::A_TILE + t * Cf::B_TILE, &tmB, &stage_full[st], (kc + u) * kBK, n0, p);
+              }
           }
         }
       }
@@ -220,8 +227,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           mbar_wait(&stage_full[j % stages], (uint32_t)((j / stages) & 1), a.wait_limit / 8);
       }
     }
-  } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer
+  } else if (warp >= 1 && warp <= kMmaWarps) {
+    // ------------------------------------------------------------ MMA issuers
+    const int myj = warp - 1;   // job of each sweep issued by this warp
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16_f32(128, Cf::BN);
       long it = 0, tloc = 0;
@@ -232,22 +240,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int sw = 0; sw < a.nsweeps && ok; ++sw) {
           const Sweep S = sched[sw];
           const int nj = S.L[1] ? 2 : 1;
-          uint32_t dcol[2];
-          int sl[2];
-          for (int j = 0; j < nj; ++j) {
-            const uint32_t e = srow[jj + j];
-            const int slot = (int)(e & 3u);
-            sl[j] = slot;
-            dcol[j] = tmem + (uint32_t)(slot * Cf::BN);
+          const bool mine = myj < nj;   // this warp has a job in the sweep
+          int slot = 0;
+          uint32_t dcol = 0;
+          if (mine) {
+            const uint32_t e = srow[jj + myj];
+            slot = (int)(e & 3u);
+            dcol = tmem + (uint32_t)(slot * Cf::BN);
             if (aborted(abortp) || !mbar_wait(&slot_empty[slot], ((e >> 2) & 1u) ^ 1u, a.wait_limit)) {
               if (!aborted(abortp)) raise_timeout(a, abortp);
               ok = false;
               break;
             }
           }
-          if (!ok) break;
           tc_fence_after();
-          for (int kc = S.k0c; kc < S.k1c; ++kc, ++it) {
+          const int np = S.nplanes;
+          for (int kc = S.k0c; kc < S.k1c; kc += S.kcs, ++it) {
+            const int nu = S.k1c - kc < S.kcs ? S.k1c - kc : S.kcs;
             const int st = (int)(it % stages);
             if (aborted(abortp) || !mbar_wait(&stage_full[st], (uint32_t)((it / stages) & 1), a.wait_limit)) {
               if (!aborted(abortp)) raise_timeout(a, abortp);
@@ -255,33 +264,38 @@ __global__ void __launch_bounds__(kThreads, 1)
               break;
             }
             tc_fence_after();
+            // descriptors of the stage's first A and B tiles; a tile or a K=16
+            // step further is a plain add on the start-address field (addr >> 4,
+            // 14 bits, no carry: shared memory addresses stay below 256 KB)
             const uint32_t base = smem_u32(smem + (size_t)st * stage_bytes);
-            for (int j = 0; j < nj; ++j) {
-              const int L = S.L[j];
-              const int pb = S.pb[j];
-              const int pe = S.pe[j];
+            const uint64_t dA0 = umma_desc(base, kRowBytes, kSwizzleCode);
+            const uint64_t dB0 = umma_desc(base + (uint32_t)s * Cf::A_TILE, kRowBytes, kSwizzleCode);
+            for (int u = 0; u < nu && mine; ++u) {
+              const int L = S.L[myj];
+              const int pb = S.pb[myj];
+              const int pe = S.pe[myj];
+              const bool first = kc + u == S.k0c;
               for (int p = pb; p <= pe; ++p) {
                 const int q = L - p;
-                const uint32_t aa = base + (uint32_t)(p - 1) * Cf::A_TILE;
-                const uint32_t ba = base + (uint32_t)s * Cf::A_TILE + (uint32_t)(q - 1) * Cf::B_TILE;
+                const uint64_t da = dA0 + (uint64_t)((u * np + p - 1) * (Cf::A_TILE >> 4));
+                const uint64_t db = dB0 + (uint64_t)((u * np + q - 1) * (Cf::B_TILE >> 4));
 #pragma unroll
                 for (int kk = 0; kk < kBK / 16; ++kk) {
-                  const uint32_t acc = (kc != S.k0c || p != pb || kk != 0) ? 1u : 0u;
-                  mma_bf16(dcol[j], umma_desc(aa + kk * 32, kRowBytes, kSwizzleCode),
-                           umma_desc(ba + kk * 32, kRowBytes, kSwizzleCode), idesc, acc);
+                  const uint32_t acc = (!first || p != pb || kk != 0) ? 1u : 0u;
+                  mma_bf16(dcol, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, acc);
                 }
               }
             }
-            mma_commit(&stage_empty[st]);
+            mma_commit(&stage_empty[st]);   // also by a warp without a job here: the stage needs both
           }
           if (!ok) break;
-          for (int j = 0; j < nj; ++j) mma_commit(&slot_full[sl[j]]);
+          if (mine) mma_commit(&slot_full[slot]);
           jj += nj;
         }
       }
       // every MMA issued by this thread must be complete before TMEM is released
-      mma_commit(&mma_done);
-      mbar_wait(&mma_done, 0, a.wait_limit);
+      mma_commit(&mma_done[myj]);
+      mbar_wait(&mma_done[myj], 0, a.wait_limit);
     }
   }
   } else {
