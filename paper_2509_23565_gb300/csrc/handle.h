@@ -28,6 +28,7 @@ struct emul_handle_s {
   std::string last_error;
   void* encode_fn = nullptr;        // cuTensorMapEncodeTiled
   long long wait_limit = 2000000000LL;
+  uint32_t leaf_salt = 0;            // epoch salt of the LU leaf exchange (per leaf launch)
   // profiling (emul_profile_*)
   long long launches = 0;
   bool prof = false;

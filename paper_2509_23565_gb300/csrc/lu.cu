@@ -31,11 +31,40 @@ constexpr int kStatusTimeout = -4;
 constexpr size_t kAl = 256;
 inline size_t al(size_t x) { return (x + kAl - 1) / kAl * kAl; }
 
-// Grid barrier of the cooperative leaf launch: a monotonic arrival counter,
-// zeroed before the launch; barrier number i completes when it reaches (i + 1) G.
-struct GridBar {
-  unsigned long long count;
-};
+// Pivot exchange of the leaf: every block publishes its candidate as 8-byte
+// words {32-bit payload, 32-bit epoch}; an aligned 64-bit store is
+// single-copy atomic, so a reader that sees the epoch of the current column in
+// a word also sees that word's payload, and no fence or counter is needed.
+// Record of block b for column parity par: words [0, 4) = |value| low and high
+// halves, candidate row, unused; words [4, 4 + 2w) = the candidate row, each
+// double as its low and high halves.  Epoch = salt * 32 + column (salt > 0,
+// distinct per leaf launch, records cleared before a factorization).
+constexpr int kRecWords = 4 + 2 * kLeaf;
+
+__device__ __forceinline__ void put_word(uint64_t* p, uint32_t payload, uint32_t epoch) {
+  *reinterpret_cast<volatile uint64_t*>(p) = (static_cast<uint64_t>(epoch) << 32) | payload;
+}
+// Two adjacent words (16-byte aligned) in one load; each stays single-copy atomic.
+__device__ __forceinline__ void get_pair(const uint64_t* p, uint64_t& a, uint64_t& b) {
+  asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p));
+}
+__device__ __forceinline__ bool has_epoch(uint64_t v, uint32_t epoch) { return static_cast<uint32_t>(v >> 32) == epoch; }
+// Poll a pair of words until both carry `epoch` (bounded); the double they
+// hold (low half first) is returned in x.  False on timeout.
+__device__ __forceinline__ bool wait_pair(const uint64_t* p, uint32_t epoch, double& x, long long limit) {
+  uint64_t a, b;
+  get_pair(p, a, b);
+  if (!(has_epoch(a, epoch) && has_epoch(b, epoch))) {
+    const long long t0 = clock64();
+    do {
+      if (clock64() - t0 > limit) return false;
+      get_pair(p, a, b);
+    } while (!(has_epoch(a, epoch) && has_epoch(b, epoch)));
+  }
+  x = __longlong_as_double(static_cast<long long>((b << 32) | (a & 0xFFFFFFFFull)));
+  return true;
+}
+constexpr int kMaxRecPerLane = 8;   // records polled by one lane: the leaf runs at most 256 blocks
 
 __device__ __forceinline__ uint64_t absbits(double x) {
   return static_cast<uint64_t>(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFull;
@@ -50,36 +79,39 @@ __device__ __forceinline__ bool better(uint64_t v1, int r1, uint64_t v2, int r2)
 // Leaf panel: rows d0..n-1, columns d0..d0+w-1 of A, factored in place with
 // partial pivoting.  Block b keeps panel rows [b*R, b*R+R) in shared memory.
 //
-// Column c: (1) pivot search on column c over the block's rows, (2) the block's
-// candidate row and row c published, (3) arrival at the grid barrier, (4) while
-// the other blocks arrive, the rank-1 update of pivot c-1 on columns c+1..w-1,
-// (5) barrier wait, global pivot and pivot-row fetch, (6) row interchange,
-// (7) multipliers of column c and the update of column c+1 only, so that the
-// next pivot search can start.  Each entry receives the same FMAs in the same
-// order as in a plain right-looking elimination; the published rows get the
-// deferred update of pivot c-1 applied on the fly (the same FMA).
+// Column c: (1) pivot search on column c over the block's rows, (2) the
+// block's candidate (|value|, row, the row itself) and, from the block owning
+// it, row c published as epoch-tagged words, (3) warp 0 collects the G
+// candidates and fetches the winner's row, the last warp fetches row c, while
+// warps 1-6 apply the rank-1 update of pivot c-1 to columns c+1..w-1,
+// (4) row interchange, (5) multipliers of column c and the update of column
+// c+1 only, so that the next pivot search can start.  Each entry receives the
+// same FMAs in the same order as in a plain right-looking elimination; the
+// published rows get the deferred update of pivot c-1 applied on the fly (the
+// same FMA).  The exchange needs no grid barrier: a block cannot publish
+// column c+2 into the slot of column c before every block has published
+// column c+1, which each does only after reading column c.
 //
 // Every interchange is also applied to the columns [pc0, d0) and [d0+w, pc1) of
 // the enclosing panel, which live in global memory: the outside column q
 // (0-based over both ranges) belongs to block q % G for the whole launch, to
-// the (q / G)-th of its threads other than thread 0 (it writes the block's
-// candidate) and the barrier lane (first lane of the last warp, which drives
-// the grid barrier and takes no part in the deferred update), so successive
+// the (q / G)-th of its threads other than thread 0 (it publishes the block's
+// candidate) and the row-c reader (first lane of the last warp), so successive
 // interchanges of one element stay in program order.  Its loads are issued
 // when the pivot is known, its stores when the next pivot is known, off the
 // critical path.  At most 248 outside columns exist (panel <= 256 wide, leaf
 // >= 8 wide); 254 owners per block are available.
 __global__ void __launch_bounds__(kLeafThreads) getf2_leaf_kernel(double* A, long lda, int n, int d0, int w, int R,
                                                                  int pc0, int pc1, int32_t* ipiv, int32_t* info,
-                                                                 GridBar* gb, double* cand_rows, uint64_t* cand_val,
-                                                                 int* cand_idx, double* diag_rows, int* status,
-                                                                 long long limit) {
+                                                                 uint64_t* recs, uint64_t* drec, uint32_t salt,
+                                                                 int* status, long long limit) {
   extern __shared__ double P[];   // P[c*R + lr]
   __shared__ double prow[2][kLeaf], crow[kLeaf];
   __shared__ double rcp_s;
   __shared__ uint64_t red_v[kLeafThreads / 32];
   __shared__ int red_r[kLeafThreads / 32];
-  __shared__ int win_s, ok_s;
+  __shared__ int win_s, ok_s, ok7_s;
+  constexpr int kRowTid = kLeafThreads - 32;   // first lane of the last warp: row-c reader
   const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int mp = n - d0;
@@ -87,8 +119,7 @@ __global__ void __launch_bounds__(kLeafThreads) getf2_leaf_kernel(double* A, lon
   const int rcount = mp - r0 < R ? (mp - r0 > 0 ? mp - r0 : 0) : R;
   const int nleft = d0 - pc0;
   const int nout = nleft + (pc1 - d0 - w);
-  constexpr int kBarTid = kLeafThreads - 32;   // barrier lane
-  const int ot = (tid == 0 || tid == kBarTid) ? -1 : tid - 1 - (tid > kBarTid ? 1 : 0);
+  const int ot = (tid == 0 || tid == kRowTid) ? -1 : tid - 1 - (tid > kRowTid ? 1 : 0);
   const int q = ot * G + b;
   double* ocol = ot >= 0 && q < nout ? A + static_cast<long>(q < nleft ? pc0 + q : d0 + w + (q - nleft)) * lda : nullptr;
   long sw_c = -1, sw_p = -1;   // pending interchange of this thread's outside column
@@ -100,7 +131,11 @@ __global__ void __launch_bounds__(kLeafThreads) getf2_leaf_kernel(double* A, lon
 
   for (int c = 0; c < w; ++c) {
     const int par = c & 1;
+    const uint32_t ep = (salt << 5) | static_cast<uint32_t>(c);
     const double* pv = prow[par ^ 1];   // pivot row of column c-1
+    uint64_t* rec_all = recs + static_cast<long>(par) * G * kRecWords;
+    uint64_t* my = rec_all + static_cast<long>(b) * kRecWords;
+    uint64_t* drow = drec + par * 2 * kLeaf;
     // (1) local candidate for column c over own rows with panel row >= c
     uint64_t bv = 0;
     int br = 0x7FFFFFFF;
@@ -133,74 +168,75 @@ __global__ void __launch_bounds__(kLeafThreads) getf2_leaf_kernel(double* A, lon
           bv = red_v[i];
           br = red_r[i];
         }
-      cand_val[par * G + b] = bv;
-      cand_idx[par * G + b] = br;
+      put_word(my + 0, static_cast<uint32_t>(bv), ep);
+      put_word(my + 1, static_cast<uint32_t>(bv >> 32), ep);
+      put_word(my + 2, static_cast<uint32_t>(br), ep);
       win_s = br;
     }
     __syncthreads();
     // (2) publish the candidate row and row c, current through pivot c-1
     {
       const int pr = win_s;
-      if (pr != 0x7FFFFFFF) {
-        const int lr = pr - r0;
-        for (int cc = tid; cc < w; cc += blockDim.x) {
+      if (tid < 2 * w) {
+        const int cc = tid >> 1;
+        if (pr != 0x7FFFFFFF) {
+          const int lr = pr - r0;
           double v = P[cc * R + lr];
           if (pend && cc > c) v = fma(-P[(c - 1) * R + lr], pv[cc], v);
-          cand_rows[(static_cast<long>(par) * G + b) * kLeaf + cc] = v;
+          const uint64_t bits = static_cast<uint64_t>(__double_as_longlong(v));
+          put_word(my + 4 + tid, static_cast<uint32_t>(tid & 1 ? bits >> 32 : bits), ep);
         }
-      }
-      if (c >= r0 && c < r0 + rcount) {
-        const int lr = c - r0;
-        for (int cc = tid; cc < w; cc += blockDim.x) {
+        if (c >= r0 && c < r0 + rcount) {
+          const int lr = c - r0;
           double v = P[cc * R + lr];
           if (pend && cc > c) v = fma(-P[(c - 1) * R + lr], pv[cc], v);
-          diag_rows[par * kLeaf + cc] = v;
+          const uint64_t bits = static_cast<uint64_t>(__double_as_longlong(v));
+          put_word(drow + tid, static_cast<uint32_t>(tid & 1 ? bits >> 32 : bits), ep);
         }
       }
     }
-    // (3) arrive (barrier lane), (4) deferred rank-1 update of pivot c-1 on
-    // columns c+1..w-1 (the other warps), (5) wait
     __syncthreads();
-    if (tid == kBarTid) {
-      const unsigned long long target = static_cast<unsigned long long>(c + 1) * G;
-      __threadfence();
-      bool ok = true;
-      if (atomicAdd(&gb->count, 1ull) + 1 < target) {
-        volatile unsigned long long* vc = &gb->count;
-        const long long t0 = clock64();
-        while (*vc < target) {
-          if (clock64() - t0 > limit) {
-            ok = false;
-            atomicExch(status, kStatusTimeout);
-            break;
-          }
-        }
-      }
-      __threadfence();
-      ok_s = ok;
-    } else if (tid < kBarTid && pend && c + 1 < w) {
-      for (int lr = tid; lr < rcount; lr += kBarTid) {
-        if (r0 + lr <= c - 1) continue;
-        const double l = P[(c - 1) * R + lr];
-        for (int cc = c + 1; cc < w; ++cc) P[cc * R + lr] = fma(-l, pv[cc], P[cc * R + lr]);
-      }
-    }
-    __syncthreads();
-    if (!ok_s) return;
-    // global pivot: warp 0 scans the G candidates and fetches the pivot row,
-    // warp 1 fetches row c
+    // (3) exchange (warp 0: candidates and pivot row; last warp: row c) while
+    // warps 1-6 apply the deferred update of pivot c-1
     if (warp == 0) {
-      const volatile uint64_t* cv = cand_val + par * G;
-      const volatile int* ci = cand_idx + par * G;
+      // every lane loads all of its records at once, then re-polls the late ones
+      uint64_t w0[kMaxRecPerLane], w1[kMaxRecPerLane], w2[kMaxRecPerLane];
+      unsigned pending = 0;
+#pragma unroll
+      for (int k = 0; k < kMaxRecPerLane; ++k)
+        if (lane + 32 * k < G) pending |= 1u << k;
+      bool ok = true;
+      const long long t0 = clock64();
+      while (true) {
+#pragma unroll
+        for (int k = 0; k < kMaxRecPerLane; ++k)
+          if (pending >> k & 1u) {
+            const uint64_t* r = rec_all + static_cast<long>(lane + 32 * k) * kRecWords;
+            uint64_t unused;
+            get_pair(r, w0[k], w1[k]);
+            get_pair(r + 2, w2[k], unused);
+          }
+#pragma unroll
+        for (int k = 0; k < kMaxRecPerLane; ++k)
+          if ((pending >> k & 1u) && has_epoch(w0[k], ep) && has_epoch(w1[k], ep) && has_epoch(w2[k], ep))
+            pending &= ~(1u << k);
+        if (__all_sync(0xFFFFFFFFu, pending == 0)) break;
+        if (__any_sync(0xFFFFFFFFu, clock64() - t0 > limit)) {
+          ok = false;
+          break;
+        }
+      }
       uint64_t gv = 0;
       int gr = 0x7FFFFFFF, gbk = 0;
-      for (int i = lane; i < G; i += 32) {
-        const uint64_t v = cv[i];
-        const int r = ci[i];
-        if (better(v, r, gv, gr)) {
+#pragma unroll
+      for (int k = 0; k < kMaxRecPerLane; ++k) {
+        if (lane + 32 * k >= G) continue;
+        const uint64_t v = ((w1[k] & 0xFFFFFFFFull) << 32) | (w0[k] & 0xFFFFFFFFull);
+        const int rr = static_cast<int>(static_cast<uint32_t>(w2[k]));
+        if (better(v, rr, gv, gr)) {
           gv = v;
-          gr = r;
-          gbk = i;
+          gr = rr;
+          gbk = lane + 32 * k;
         }
       }
 #pragma unroll
@@ -214,22 +250,44 @@ __global__ void __launch_bounds__(kLeafThreads) getf2_leaf_kernel(double* A, lon
           gbk = b2;
         }
       }
-      if (lane < w) {
-        const double pvv = static_cast<const volatile double*>(cand_rows)[(static_cast<long>(par) * G + gbk) * kLeaf + lane];
+      if (ok && lane < w) {
+        double pvv = 0.0;
+        ok = wait_pair(rec_all + static_cast<long>(gbk) * kRecWords + 4 + 2 * lane, ep, pvv, limit);
         prow[par][lane] = pvv;
         if (lane == c) rcp_s = 1.0 / pvv;
       }
+      ok = __all_sync(0xFFFFFFFFu, ok);
       if (lane == 0) {
         win_s = gr;
-        if (b == 0) {
+        ok_s = ok;
+        if (!ok) atomicExch(status, kStatusTimeout);
+        if (ok && b == 0) {
           ipiv[d0 + c] = d0 + gr + 1;
           if (gv == 0) atomicCAS(info, 0, d0 + c + 1);
         }
       }
-    } else if (warp == 1) {
-      if (lane < w) crow[lane] = static_cast<const volatile double*>(diag_rows)[par * kLeaf + lane];
+    } else if (warp == kLeafThreads / 32 - 1) {
+      bool ok = true;
+      if (lane < w) {
+        double x = 0.0;
+        ok = wait_pair(drow + 2 * lane, ep, x, limit);
+        crow[lane] = x;
+      }
+      ok = __all_sync(0xFFFFFFFFu, ok);
+      if (lane == 0) {
+        ok7_s = ok;
+        if (!ok) atomicExch(status, kStatusTimeout);
+      }
+    } else if (pend && c + 1 < w) {
+      constexpr int kUpd = kLeafThreads - 64;   // warps 1-6
+      for (int lr = tid - 32; lr < rcount; lr += kUpd) {
+        if (r0 + lr <= c - 1) continue;
+        const double l = P[(c - 1) * R + lr];
+        for (int cc = c + 1; cc < w; ++cc) P[cc * R + lr] = fma(-l, pv[cc], P[cc * R + lr]);
+      }
     }
     __syncthreads();
+    if (!ok_s || !ok7_s) return;
     const int p = win_s;
     if (ocol) {
       if (sw_c >= 0) {
@@ -247,7 +305,7 @@ __global__ void __launch_bounds__(kLeafThreads) getf2_leaf_kernel(double* A, lon
     const double piv = prow[par][c];
     pend = piv != 0.0;
     if (pend) {
-      // (6) interchange rows c and p (both current through pivot c-1)
+      // (4) interchange rows c and p (both current through pivot c-1)
       if (p != c) {
         if (c >= r0 && c < r0 + rcount)
           for (int cc = tid; cc < w; cc += blockDim.x) P[cc * R + (c - r0)] = prow[par][cc];
@@ -255,7 +313,7 @@ __global__ void __launch_bounds__(kLeafThreads) getf2_leaf_kernel(double* A, lon
           for (int cc = tid; cc < w; cc += blockDim.x) P[cc * R + (p - r0)] = crow[cc];
       }
       __syncthreads();
-      // (7) multipliers of column c, update of column c+1
+      // (5) multipliers of column c, update of column c+1
       const bool use_rcp = fabs(piv) >= 2.2250738585072014e-308;
       const double rcp = rcp_s;
       const double u1 = c + 1 < w ? prow[par][c + 1] : 0.0;
@@ -646,11 +704,8 @@ __global__ void probe_check_kernel(int m, int n, int k, const double* L, long ld
 // ------------------------------------------------------------------ host helpers
 struct LuBufs {
   double* inv;          // nb x nb
-  double* cand_rows;    // [2][G][kLeaf]
-  uint64_t* cand_val;   // [2][G]
-  int* cand_idx;        // [2][G]
-  double* diag_rows;    // [2][kLeaf]
-  GridBar* bar;
+  uint64_t* recs;       // leaf pivot exchange: [2][nsm][kRecWords] epoch-tagged words
+  uint64_t* drec;       // [2][2 kLeaf]: row c of the leaf, epoch-tagged words
   unsigned long long* racc;
   int* map;             // laswp gather maps, [4*kPermMax + 1] ints each, one per recursion depth
   double* probe;        // y0, a0, y1, a1 (kProbeRows each), z, za (nb each)
@@ -659,9 +714,11 @@ struct LuBufs {
 constexpr int kMapInts = 4 * kPermMax + 8;
 constexpr int kMaxDepth = 8;
 
+size_t rec_bytes(int nsm) { return 2ull * nsm * kRecWords * 8; }
+
 size_t lu_extra_bytes(int nb, int nsm) {
-  return al(static_cast<size_t>(nb) * nb * 8) + al(2ull * nsm * kLeaf * 8) + al(2ull * nsm * 8) + al(2ull * nsm * 4) +
-         al(2ull * kLeaf * 8) + al(sizeof(GridBar)) + al(4 * 8) + al(kMaxDepth * kMapInts * 4) +
+  return al(static_cast<size_t>(nb) * nb * 8) + al(rec_bytes(nsm)) + al(2ull * 2 * kLeaf * 8) + al(4 * 8) +
+         al(kMaxDepth * kMapInts * 4) +
          al((4ull * kProbeRows + 2ull * nb) * 8) + al(16) + kAl;
 }
 
@@ -670,16 +727,10 @@ LuBufs carve(emul_handle_t h, size_t off, int nb) {
   LuBufs b;
   b.inv = reinterpret_cast<double*>(p);
   p += al(static_cast<size_t>(nb) * nb * 8);
-  b.cand_rows = reinterpret_cast<double*>(p);
-  p += al(2ull * h->nsm * kLeaf * 8);
-  b.cand_val = reinterpret_cast<uint64_t*>(p);
-  p += al(2ull * h->nsm * 8);
-  b.cand_idx = reinterpret_cast<int*>(p);
-  p += al(2ull * h->nsm * 4);
-  b.diag_rows = reinterpret_cast<double*>(p);
-  p += al(2ull * kLeaf * 8);
-  b.bar = reinterpret_cast<GridBar*>(p);
-  p += al(sizeof(GridBar));
+  b.recs = reinterpret_cast<uint64_t*>(p);
+  p += al(rec_bytes(h->nsm));
+  b.drec = reinterpret_cast<uint64_t*>(p);
+  p += al(2ull * 2 * kLeaf * 8);
   b.racc = reinterpret_cast<unsigned long long*>(p);
   p += al(4 * 8);
   b.map = reinterpret_cast<int*>(p);
@@ -698,11 +749,10 @@ int launch_leaf(emul_handle_t h, double* A, long lda, int n, int d0, int w, int 
   if ((mp + G - 1) / G > smem_rows_cap) G = (mp + smem_rows_cap - 1) / smem_rows_cap;
   if (G < 1) G = 1;
   if (G > h->nsm) G = h->nsm;
+  if (G > 32 * kMaxRecPerLane) G = 32 * kMaxRecPerLane;
   const int R = (mp + G - 1) / G;
   const size_t smem = static_cast<size_t>(R) * w * 8;
   if (smem > 220 * 1024) return set_error(h, EMUL_NOT_SUPPORTED, "panel too tall for the leaf kernel");
-  int rc = check_cuda(h, cudaMemsetAsync(B.bar, 0, sizeof(GridBar), h->stream), "barrier reset");
-  if (rc) return rc;
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(getf2_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
@@ -710,9 +760,12 @@ int launch_leaf(emul_handle_t h, double* A, long lda, int n, int d0, int w, int 
   }
   long long limit = h->wait_limit;
   int* status = h->d_status;
+  // epochs of this launch: (salt << 5) | column, salt > 0 and new per launch
+  // (the records are cleared and the salt restarted by every factorization)
+  uint32_t salt = ++h->leaf_salt;
+  if (salt >= (1u << 27)) return set_error(h, EMUL_NOT_SUPPORTED, "too many panel leaves in one factorization");
   void* args[] = {&A, const_cast<long*>(&lda), &n, &d0, &w, const_cast<int*>(&R), &pc0, &pc1, &ipiv, &info,
-                  const_cast<GridBar**>(&B.bar), const_cast<double**>(&B.cand_rows), const_cast<uint64_t**>(&B.cand_val),
-                  const_cast<int**>(&B.cand_idx), const_cast<double**>(&B.diag_rows), &status, &limit};
+                  const_cast<uint64_t**>(&B.recs), const_cast<uint64_t**>(&B.drec), &salt, &status, &limit};
   h->launches++;
   return check_cuda(h,
                     cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(getf2_leaf_kernel), dim3(G),
@@ -816,6 +869,11 @@ int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int n
   rc = emul::reserve_workspace(h, gw + emul::lu_extra_bytes(nb, h->nsm));
   if (rc) return rc;
   const emul::LuBufs B = emul::carve(h, gw, nb);
+  rc = emul::check_cuda(h, cudaMemsetAsync(B.recs, 0, emul::rec_bytes(h->nsm), h->stream), "leaf records");
+  if (rc) return rc;
+  rc = emul::check_cuda(h, cudaMemsetAsync(B.drec, 0, 2ull * 2 * emul::kLeaf * 8, h->stream), "leaf records");
+  if (rc) return rc;
+  h->leaf_salt = 0;
   for (int j0 = 0; j0 < n; j0 += nb) {
     const int jb = nb < n - j0 ? nb : n - j0;
     rc = emul::rgetrf(h, A, lda, n, j0, jb, j0, j0 + jb, ipiv, info, autos ? s_prev : s_fixed, B);
