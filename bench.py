@@ -242,6 +242,7 @@ def run_ours(args, world, rank, local):
                    "l2": "inputs (8 n^2 bytes) larger than L2; each step restores A from a device copy"},
         "backward_error": float(berr[1]), "scaled_residual_eq8": float(berr[0]), "info": info_v,
         "roofline": roofline, "gpu_launches": int(prof["kernel_launches"]), "clocks": clk,
+        "phases_ms_per_step": {k: round(v / args.steps, 2) for k, v in prof["phase_ms"].items()},
     }
 
     if rank == 0 and not args.no_e2e:

@@ -247,9 +247,24 @@ typedef struct emul_profile {
   double product_ms;            /* their summed device time (CUDA events) */
   double product_tensor_flops;  /* sum of 2 m n k P (P = s(s+1)/2 slice-pair products) */
   double product_bytes;         /* algorithmic bytes: C read + write (8 B each) and the slices read */
+  double phase_ms[5];           /* device time of the factorization phases (CUDA events around each),
+                                   indexed by EMUL_PHASE_* */
 } emul_profile;
 
-/* Enable (1) or disable (0) event timing of the product kernel. */
+/* Phases of emul_dgetrf / emul_dgetrs timed when profiling is enabled:
+ * PANEL  the panel factorization (leaves, inner products, small solves),
+ * SWAP   the panel's row interchanges applied to the columns outside it,
+ * U12    L11^-1 and U12 = L11^-1 A12,
+ * UPDATE the trailing update A22 - L21 U12 (slicing, product, selector probe),
+ * SOLVE  emul_dgetrs. */
+#define EMUL_PHASE_PANEL 0
+#define EMUL_PHASE_SWAP 1
+#define EMUL_PHASE_U12 2
+#define EMUL_PHASE_UPDATE 3
+#define EMUL_PHASE_SOLVE 4
+
+/* Enable (1) or disable (0) event timing of the product kernel and of the
+ * factorization phases. */
 int emul_profile_enable(emul_handle_t h, int enable);
 /* Synchronise the handle's stream, return the counters and reset them. */
 int emul_profile_read(emul_handle_t h, emul_profile* out);

@@ -69,7 +69,9 @@ class Stats(ctypes.Structure):
 class Profile(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_longlong), ("product_launches", ctypes.c_longlong),
                 ("product_ms", ctypes.c_double), ("product_tensor_flops", ctypes.c_double),
-                ("product_bytes", ctypes.c_double)]
+                ("product_bytes", ctypes.c_double), ("phase_ms", ctypes.c_double * 5)]
+
+PHASES = ("panel", "swap", "u12", "update", "solve")   # EMUL_PHASE_* order
 
 
 def load():
@@ -158,7 +160,9 @@ class Emul:
     def profile_read(self):
         p = Profile()
         self._check(self.lib.emul_profile_read(self.h, ctypes.byref(p)), "emul_profile_read")
-        return {k: getattr(p, k) for k, _ in Profile._fields_}
+        out = {k: getattr(p, k) for k, _ in Profile._fields_ if k != "phase_ms"}
+        out["phase_ms"] = {name: float(p.phase_ms[i]) for i, name in enumerate(PHASES)}
+        return out
 
     def workspace_bytes(self):
         return int(self.lib.emul_workspace_bytes(self.h))

@@ -513,6 +513,38 @@ int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Oper
 
 using emul::Operand;
 
+namespace emul {
+
+namespace {
+bool pool_event(emul_handle_t h, cudaEvent_t* ev) {
+  if (!h->event_pool.empty()) {
+    *ev = h->event_pool.back();
+    h->event_pool.pop_back();
+    return true;
+  }
+  return cudaEventCreate(ev) == cudaSuccess;
+}
+}  // namespace
+
+int phase_begin(emul_handle_t h, int kind) {
+  if (!h->prof) return -1;
+  emul_handle_s::PhaseRec r{kind, nullptr, nullptr};
+  if (!pool_event(h, &r.e0)) return -1;
+  if (!pool_event(h, &r.e1)) {
+    h->event_pool.push_back(r.e0);
+    return -1;
+  }
+  cudaEventRecord(r.e0, h->stream);
+  h->phases.push_back(r);
+  return static_cast<int>(h->phases.size()) - 1;
+}
+
+void phase_end(emul_handle_t h, int idx) {
+  if (idx >= 0 && idx < static_cast<int>(h->phases.size())) cudaEventRecord(h->phases[idx].e1, h->stream);
+}
+
+}  // namespace emul
+
 extern "C" {
 
 int emul_create(emul_handle_t* handle, void* stream) {
@@ -548,6 +580,10 @@ int emul_destroy(emul_handle_t h) {
   cudaStreamSynchronize(h->stream);
   for (auto& kv : h->sched_cache) cudaFree(kv.second.sched);
   for (auto& r : h->recs) {
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+  }
+  for (auto& r : h->phases) {
     cudaEventDestroy(r.e0);
     cudaEventDestroy(r.e1);
   }
@@ -605,6 +641,13 @@ int emul_profile_read(emul_handle_t h, emul_profile* out) {
     h->event_pool.push_back(r.e1);
   }
   h->recs.clear();
+  for (auto& r : h->phases) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess && r.kind >= 0 && r.kind < 5) p.phase_ms[r.kind] += ms;
+    h->event_pool.push_back(r.e0);
+    h->event_pool.push_back(r.e1);
+  }
+  h->phases.clear();
   h->launches = 0;
   *out = p;
   return EMUL_OK;

@@ -37,6 +37,11 @@ struct emul_handle_s {
     double flops, bytes;
   };
   std::vector<ProfRec> recs;
+  struct PhaseRec {
+    int kind;
+    cudaEvent_t e0, e1;
+  };
+  std::vector<PhaseRec> phases;
   std::vector<cudaEvent_t> event_pool;
   void* selector = nullptr;         // emul::SelectorState (selector.cu)
   void* batched = nullptr;          // emul::BatchedState (batched.cu)
@@ -55,6 +60,11 @@ int check_cuda(emul_handle_t h, cudaError_t e, const char* what);
 
 // Grow the workspace to at least `bytes` (synchronises the device when it grows).
 int reserve_workspace(emul_handle_t h, size_t bytes);
+// Event timing of one factorization phase (EMUL_PHASE_*) while profiling is
+// enabled: phase_begin returns a record index (-1 when profiling is off or an
+// event cannot be had), phase_end closes it.
+int phase_begin(emul_handle_t h, int kind);
+void phase_end(emul_handle_t h, int idx);
 // Workspace bytes a product of this shape needs (slices, scales).
 size_t gemm_workspace_bytes(int m, int n, int k, int s, bool same_operand);
 

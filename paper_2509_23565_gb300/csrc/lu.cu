@@ -403,7 +403,7 @@ __global__ void laswp_perm_kernel(const int32_t* ipiv, int k1, int k2, int* map 
 // every source row into shared memory, then writes the destinations.
 constexpr int kSwpCols = 8;
 __global__ void __launch_bounds__(256) laswp_apply_kernel(double* A, long lda, int c0, int c1, const int* map) {
-  __shared__ double buf[2 * kPermMax][kSwpCols];
+  __shared__ double buf[kSwpCols][2 * kPermMax];
   __shared__ int dst_s[2 * kPermMax], src_s[2 * kPermMax];
   const int cnt = map[4 * kPermMax];
   for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
@@ -412,23 +412,26 @@ __global__ void __launch_bounds__(256) laswp_apply_kernel(double* A, long lda, i
   }
   __syncthreads();
   const int cb = c0 + blockIdx.x * kSwpCols;
-  for (int e = threadIdx.x; e < cnt * kSwpCols; e += blockDim.x) {
-    const int i = e % cnt, j = e / cnt;
-    if (cb + j < c1) buf[i][j] = A[src_s[i] + static_cast<long>(cb + j) * lda];
+  const int ncol = c1 - cb < kSwpCols ? c1 - cb : kSwpCols;
+  for (int j = 0; j < ncol; ++j) {
+    const double* col = A + static_cast<long>(cb + j) * lda;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) buf[j][i] = col[src_s[i]];
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < cnt * kSwpCols; e += blockDim.x) {
-    const int i = e % cnt, j = e / cnt;
-    if (cb + j < c1) A[dst_s[i] + static_cast<long>(cb + j) * lda] = buf[i][j];
+  for (int j = 0; j < ncol; ++j) {
+    double* col = A + static_cast<long>(cb + j) * lda;
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) col[dst_s[i]] = buf[j][i];
   }
 }
 
 // X (w1 x w2 at A[d0.., c0..]) <- L^-1 X with L unit lower w1 x w1 at A[d0.., d0..]
 // (w1 <= 128).  The strictly lower part of L is staged in shared memory; one
-// warp per column of X, lane l holding rows l, l+32, l+64, l+96 in registers,
-// x_k broadcast by shuffle.
+// warp per column of X (cpb columns per block), lane l holding rows l, l+32,
+// l+64, l+96 in registers, x_k broadcast by shuffle.
 constexpr int kTrsmMax = 128;
-__global__ void __launch_bounds__(256) trsm_small_kernel(double* A, long lda, int d0, int w1, int c0, int w2) {
+__global__ void __launch_bounds__(256) trsm_small_kernel(double* A, long lda, int d0, int w1, int c0, int w2,
+                                                         int cpb) {
+  // all threads stage L; the first cpb warps solve one column of X each
   extern __shared__ double Ls[];   // Ls[i + k*w1] = L(i, k) for i > k, else 0
   const int tid = threadIdx.x, lane = tid & 31;
   for (int e = tid; e < w1 * w1; e += blockDim.x) {
@@ -436,7 +439,8 @@ __global__ void __launch_bounds__(256) trsm_small_kernel(double* A, long lda, in
     Ls[e] = i > k ? A[(d0 + i) + static_cast<long>(d0 + k) * lda] : 0.0;
   }
   __syncthreads();
-  const int j = blockIdx.x * (blockDim.x / 32) + (tid >> 5);
+  if ((tid >> 5) >= cpb) return;
+  const int j = blockIdx.x * cpb + (tid >> 5);
   if (j >= w2) return;
   double* col = A + static_cast<long>(c0 + j) * lda + d0;
   double x[4];
@@ -514,37 +518,62 @@ __global__ void potf2_kernel(double* A, long lda, int d0, int nb, int32_t* info)
   }
 }
 
-// ------------------------------------------------------------------ solves
-// x[d0 .. d0+bs) of every right-hand side solved with the bs x bs diagonal block
-// of a triangular matrix T (lower / upper, unit / non-unit; `trans`: use T^T
-// where T is stored lower).  One block per right-hand side.
-__global__ void trsv_block_kernel(const double* T, long ldt, double* X, long ldx, int d0, int bs, int lower, int unit,
-                                  int trans) {
-  extern __shared__ double tb[];   // the bs x bs diagonal block, tb[r + c*bs] = T(d0+r, d0+c) as stored
-  __shared__ double x[128];
+// One diagonal block of a triangular solve, x <- op(T)^-1 x for the bs x bs
+// block at T[d0.., d0..] (bs <= 128; op = transpose with `trans`).  All
+// threads stage the block (leading dimension bs + 1: conflict-free either
+// way), then warp 0 solves with x in registers (lane l holds rows l, l+32,
+// l+64, l+96), each x_k divided by its diagonal entry (non-unit) and broadcast
+// by shuffle.  blockIdx.x = right-hand side.
+__global__ void __launch_bounds__(1024) trsv_block_kernel(const double* T, long ldt, double* X, long ldx, int d0,
+                                                          int bs, int lower, int unit, int trans) {
+  extern __shared__ double tb[];   // tb[r + c*(bs+1)] = T(d0+r, d0+c) as stored
+  const int ld = bs + 1;
   double* xc = X + static_cast<long>(blockIdx.x) * ldx + d0;
-  const int i = threadIdx.x;
-  for (int c = 0; c < bs; ++c)
-    if (i < bs) tb[i + c * bs] = T[(d0 + i) + static_cast<long>(d0 + c) * ldt];
-  if (i < bs) x[i] = xc[i];
-  __syncthreads();
-  auto t = [&](int r, int c) -> double { return trans ? tb[c + r * bs] : tb[r + c * bs]; };
-  if (lower) {
-    for (int k = 0; k < bs; ++k) {
-      if (!unit && i == k) x[k] = x[k] / t(k, k);
-      __syncthreads();
-      if (i > k && i < bs) x[i] = fma(-t(i, k), x[k], x[i]);
-      __syncthreads();
-    }
-  } else {
-    for (int k = bs - 1; k >= 0; --k) {
-      if (!unit && i == k) x[k] = x[k] / t(k, k);
-      __syncthreads();
-      if (i < k) x[i] = fma(-t(i, k), x[k], x[i]);
-      __syncthreads();
-    }
+  {
+    const int r = threadIdx.x & 127;
+    if (r < bs)
+      for (int c = threadIdx.x >> 7; c < bs; c += blockDim.x >> 7)
+        tb[r + c * ld] = T[(d0 + r) + static_cast<long>(d0 + c) * ldt];
   }
-  if (i < bs) xc[i] = x[i];
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  auto t = [&](int r, int c) -> double { return trans ? tb[c + r * ld] : tb[r + c * ld]; };
+  double x[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) x[q] = lane + 32 * q < bs ? xc[lane + 32 * q] : 0.0;
+  if (lower) {
+#pragma unroll
+    for (int q0 = 0; q0 < 4; ++q0)
+      for (int kk = 0; kk < 32; ++kk) {
+        const int k = 32 * q0 + kk;
+        if (k >= bs) break;
+        if (!unit && lane == kk) x[q0] = x[q0] / t(k, k);
+        const double xk = __shfl_sync(0xFFFFFFFFu, x[q0], kk);
+#pragma unroll
+        for (int q = q0; q < 4; ++q) {
+          const int i = lane + 32 * q;
+          if (i > k && i < bs) x[q] = fma(-t(i, k), xk, x[q]);
+        }
+      }
+  } else {
+#pragma unroll
+    for (int q0 = 3; q0 >= 0; --q0)
+      for (int kk = 31; kk >= 0; --kk) {
+        const int k = 32 * q0 + kk;
+        if (k >= bs) continue;
+        if (!unit && lane == kk) x[q0] = x[q0] / t(k, k);
+        const double xk = __shfl_sync(0xFFFFFFFFu, x[q0], kk);
+#pragma unroll
+        for (int q = 0; q <= q0; ++q) {
+          const int i = lane + 32 * q;
+          if (i < k) x[q] = fma(-t(i, k), xk, x[q]);
+        }
+      }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    if (lane + 32 * q < bs) xc[lane + 32 * q] = x[q];
 }
 
 // x[r] -= sum_{c in [c0, c0+bs)} T(r, c) x[c] for rows r in [r0, r1); T(r, c) =
@@ -805,7 +834,9 @@ int trsm_small(emul_handle_t h, double* A, long lda, int d0, int w1, int c0, int
     cudaFuncSetAttribute(trsm_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmMax * kTrsmMax * 8);
     attr_set = true;
   }
-  trsm_small_kernel<<<(w2 + 7) / 8, 256, static_cast<size_t>(w1) * w1 * 8, h->stream>>>(A, lda, d0, w1, c0, w2);
+  // one column per block: the solve is FP64-bound (about 1.6 FMA per clock per
+  // SM), so it is spread over as many SMs as columns; 256 threads stage L
+  trsm_small_kernel<<<w2, 256, static_cast<size_t>(w1) * w1 * 8, h->stream>>>(A, lda, d0, w1, c0, w2, 1);
   h->launches++;
   return check_cuda(h, cudaGetLastError(), "panel trsm");
 }
@@ -836,11 +867,43 @@ int rgetrf(emul_handle_t h, double* A, long lda, int n, int d0, int w, int pc0, 
 void trsv_attr() {
   static bool done = false;
   if (!done) {
-    cudaFuncSetAttribute(trsv_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 8);
+    cudaFuncSetAttribute(trsv_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 129 * 8);
     done = true;
   }
 }
 
+}  // namespace emul
+
+namespace emul {
+// Solve with the factors of emul_dgetrf (arguments validated by the caller).
+int getrs_body(emul_handle_t h, int n, int nrhs, const double* LU, int lda, const int32_t* ipiv, double* B,
+               int ldb) {
+  const size_t need = lu_extra_bytes(16, h->nsm);
+  int rc = reserve_workspace(h, need);
+  if (rc) return rc;
+  const LuBufs W = carve(h, 0, 16);
+  for (int k = 0; k < n; k += kPermMax) {
+    rc = laswp(h, B, ldb, 0, nrhs, ipiv, k, k + kPermMax < n ? k + kPermMax : n, W.map);
+    if (rc) return rc;
+  }
+  constexpr int bs = 128;  // diagonal blocks of the substitution
+  for (int d0 = 0; d0 < n; d0 += bs) {
+    const int b = bs < n - d0 ? bs : n - d0;
+    trsv_block_kernel<<<nrhs, 1024, b * (b + 1) * sizeof(double), h->stream>>>(LU, lda, B, ldb, d0, b, 1, 1, 0);
+    h->launches += (d0 + b < n) ? 2 : 1;
+    if (d0 + b < n)
+      gemv_update_kernel<<<dim3((n - d0 - b + 255) / 256, nrhs), 256, 0, h->stream>>>(LU, lda, B, ldb, d0 + b,
+                                                                                               n, d0, b, 0);
+  }
+  for (int d0 = ((n - 1) / bs) * bs; d0 >= 0; d0 -= bs) {
+    const int b = bs < n - d0 ? bs : n - d0;
+    trsv_block_kernel<<<nrhs, 1024, b * (b + 1) * sizeof(double), h->stream>>>(LU, lda, B, ldb, d0, b, 0, 0, 0);
+    h->launches += (d0 > 0) ? 2 : 1;
+    if (d0 > 0)
+      gemv_update_kernel<<<dim3((d0 + 255) / 256, nrhs), 256, 0, h->stream>>>(LU, lda, B, ldb, 0, d0, d0, b, 0);
+  }
+  return check_cuda(h, cudaGetLastError(), "getrs");
+}
 }  // namespace emul
 
 using emul::Operand;
@@ -876,16 +939,21 @@ int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int n
   h->leaf_salt = 0;
   for (int j0 = 0; j0 < n; j0 += nb) {
     const int jb = nb < n - j0 ? nb : n - j0;
+    int ph = emul::phase_begin(h, EMUL_PHASE_PANEL);
     rc = emul::rgetrf(h, A, lda, n, j0, jb, j0, j0 + jb, ipiv, info, autos ? s_prev : s_fixed, B);
+    emul::phase_end(h, ph);
     if (rc) return rc;
+    ph = emul::phase_begin(h, EMUL_PHASE_SWAP);
     rc = emul::laswp_prepare(h, ipiv, j0, j0 + jb, B.map);
     if (rc) return rc;
     rc = emul::laswp_apply(h, A, lda, 0, j0, B.map);
     if (rc) return rc;
     rc = emul::laswp_apply(h, A, lda, j0 + jb, n, B.map);
+    emul::phase_end(h, ph);
     if (rc) return rc;
     const int m2 = n - j0 - jb;
     if (m2 > 0) {
+      ph = emul::phase_begin(h, EMUL_PHASE_U12);
       emul::trtri_lower_kernel<<<jb, (jb + 31) / 32 * 32, jb * sizeof(double), h->stream>>>(A, lda, j0, jb, 1, B.inv);
       h->launches++;
       rc = emul::check_cuda(h, cudaGetLastError(), "trtri");
@@ -894,7 +962,9 @@ int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int n
       // U12 = L11^-1 A12 (jb x m2), written over A12
       rc = emul::gemm_run(h, jb, m2, jb, 1.0, Operand{B.inv, 1, jb}, Operand{A12, lda, 1}, 0.0, A12, lda,
                           autos ? s_prev : s_fixed, false, 0, nullptr, 0, 0);
+      emul::phase_end(h, ph);
       if (rc) return rc;
+      ph = emul::phase_begin(h, EMUL_PHASE_UPDATE);
       const double* L21 = A + (j0 + jb) + static_cast<long>(j0) * lda;
       double* A22 = A + (j0 + jb) + static_cast<long>(j0 + jb) * lda;
       int s_step = slices;
@@ -959,6 +1029,7 @@ int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int n
           stats->slices_max = s_step > stats->slices_max ? s_step : stats->slices_max;
         }
       }
+      emul::phase_end(h, ph);
       slices_sum += s_step;
       updates++;
       s_prev = s_step;
@@ -976,31 +1047,10 @@ int emul_dgetrs(emul_handle_t h, int n, int nrhs, const double* LU, int lda, con
   if (n < 0 || nrhs < 0 || lda < (n > 1 ? n : 1) || ldb < (n > 1 ? n : 1) || (n > 0 && nrhs > 0 && (!LU || !ipiv || !B)))
     return emul::set_error(h, EMUL_INVALID_ARG, "emul_dgetrs: invalid argument");
   if (n == 0 || nrhs == 0) return EMUL_OK;
-  const size_t need = emul::lu_extra_bytes(16, h->nsm);
-  int rc = emul::reserve_workspace(h, need);
-  if (rc) return rc;
-  const emul::LuBufs W = emul::carve(h, 0, 16);
-  for (int k = 0; k < n; k += emul::kPermMax) {
-    rc = emul::laswp(h, B, ldb, 0, nrhs, ipiv, k, k + emul::kPermMax < n ? k + emul::kPermMax : n, W.map);
-    if (rc) return rc;
-  }
-  constexpr int bs = 128;  // diagonal blocks of the substitution
-  for (int d0 = 0; d0 < n; d0 += bs) {
-    const int b = bs < n - d0 ? bs : n - d0;
-    emul::trsv_block_kernel<<<nrhs, 128, b * b * sizeof(double), h->stream>>>(LU, lda, B, ldb, d0, b, 1, 1, 0);
-    h->launches += (d0 + b < n) ? 2 : 1;
-    if (d0 + b < n)
-      emul::gemv_update_kernel<<<dim3((n - d0 - b + 255) / 256, nrhs), 256, 0, h->stream>>>(LU, lda, B, ldb, d0 + b,
-                                                                                               n, d0, b, 0);
-  }
-  for (int d0 = ((n - 1) / bs) * bs; d0 >= 0; d0 -= bs) {
-    const int b = bs < n - d0 ? bs : n - d0;
-    emul::trsv_block_kernel<<<nrhs, 128, b * b * sizeof(double), h->stream>>>(LU, lda, B, ldb, d0, b, 0, 0, 0);
-    h->launches += (d0 > 0) ? 2 : 1;
-    if (d0 > 0)
-      emul::gemv_update_kernel<<<dim3((d0 + 255) / 256, nrhs), 256, 0, h->stream>>>(LU, lda, B, ldb, 0, d0, d0, b, 0);
-  }
-  return emul::check_cuda(h, cudaGetLastError(), "getrs");
+  const int ph = emul::phase_begin(h, EMUL_PHASE_SOLVE);
+  const int rc = emul::getrs_body(h, n, nrhs, LU, lda, ipiv, B, ldb);
+  emul::phase_end(h, ph);
+  return rc;
 }
 
 int emul_dpotrf(emul_handle_t h, char uplo, int n, double* A, int lda, int nb, int slices, int32_t* info,
@@ -1055,7 +1105,7 @@ int emul_dpotrs(emul_handle_t h, char uplo, int n, int nrhs, const double* L, in
   constexpr int bs = 128;
   for (int d0 = 0; d0 < n; d0 += bs) {
     const int b = bs < n - d0 ? bs : n - d0;
-    emul::trsv_block_kernel<<<nrhs, 128, b * b * sizeof(double), h->stream>>>(L, lda, B, ldb, d0, b, 1, 0, 0);
+    emul::trsv_block_kernel<<<nrhs, 1024, b * (b + 1) * sizeof(double), h->stream>>>(L, lda, B, ldb, d0, b, 1, 0, 0);
     h->launches += (d0 + b < n) ? 2 : 1;
     if (d0 + b < n)
       emul::gemv_update_kernel<<<dim3((n - d0 - b + 255) / 256, nrhs), 256, 0, h->stream>>>(L, lda, B, ldb, d0 + b,
@@ -1063,7 +1113,7 @@ int emul_dpotrs(emul_handle_t h, char uplo, int n, int nrhs, const double* L, in
   }
   for (int d0 = ((n - 1) / bs) * bs; d0 >= 0; d0 -= bs) {
     const int b = bs < n - d0 ? bs : n - d0;
-    emul::trsv_block_kernel<<<nrhs, 128, b * b * sizeof(double), h->stream>>>(L, lda, B, ldb, d0, b, 0, 0, 1);
+    emul::trsv_block_kernel<<<nrhs, 1024, b * (b + 1) * sizeof(double), h->stream>>>(L, lda, B, ldb, d0, b, 0, 0, 1);
     h->launches += (d0 > 0) ? 2 : 1;
     if (d0 > 0)
       emul::gemv_update_kernel<<<dim3((d0 + 7) / 8, nrhs), 256, 0, h->stream>>>(L, lda, B, ldb, 0, d0, d0, b, 1);
