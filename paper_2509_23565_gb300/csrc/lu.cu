@@ -125,8 +125,18 @@ __global__ void __launch_bounds__(kLeafThreads) getf2_leaf_kernel(double* A, lon
   long sw_c = -1, sw_p = -1;   // pending interchange of this thread's outside column
   double sw_xc = 0.0, sw_xp = 0.0;
   bool pend = false;           // pivot c-1 was nonzero: its update of columns > c is pending
-  for (int c = 0; c < w; ++c)
-    for (int lr = tid; lr < rcount; lr += blockDim.x) P[c * R + lr] = A[(d0 + r0 + lr) + static_cast<long>(d0 + c) * lda];
+  // stage the rows: 16 loads in flight per thread before their stores
+  for (int lr = tid; lr < rcount; lr += blockDim.x) {
+    const double* src = A + (d0 + r0 + lr) + static_cast<long>(d0) * lda;
+    for (int c0 = 0; c0 < w; c0 += 16) {
+      double v[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = c0 + j < w ? src[static_cast<long>(c0 + j) * lda] : 0.0;
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (c0 + j < w) P[(c0 + j) * R + lr] = v[j];
+    }
+  }
   __syncthreads();
 
   for (int c = 0; c < w; ++c) {
@@ -434,9 +444,23 @@ __global__ void __launch_bounds__(256) trsm_small_kernel(double* A, long lda, in
   // all threads stage L; the first cpb warps solve one column of X each
   extern __shared__ double Ls[];   // Ls[i + k*w1] = L(i, k) for i > k, else 0
   const int tid = threadIdx.x, lane = tid & 31;
-  for (int e = tid; e < w1 * w1; e += blockDim.x) {
-    const int i = e % w1, k = e / w1;
-    Ls[e] = i > k ? A[(d0 + i) + static_cast<long>(d0 + k) * lda] : 0.0;
+  {
+    // row i per thread, columns k = tid/128 + 2j, 16 loads in flight before their stores
+    const int i = tid & 127, kstep = blockDim.x >> 7;
+    if (i < w1)
+      for (int k0 = tid >> 7; k0 < w1; k0 += 16 * kstep) {
+        double v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int k = k0 + j * kstep;
+          v[j] = (k < w1 && i > k) ? A[(d0 + i) + static_cast<long>(d0 + k) * lda] : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int k = k0 + j * kstep;
+          if (k < w1) Ls[i + k * w1] = v[j];
+        }
+      }
   }
   __syncthreads();
   if ((tid >> 5) >= cpb) return;
@@ -530,10 +554,19 @@ __global__ void __launch_bounds__(1024) trsv_block_kernel(const double* T, long 
   const int ld = bs + 1;
   double* xc = X + static_cast<long>(blockIdx.x) * ldx + d0;
   {
-    const int r = threadIdx.x & 127;
+    const int r = threadIdx.x & 127, cstep = blockDim.x >> 7;
     if (r < bs)
-      for (int c = threadIdx.x >> 7; c < bs; c += blockDim.x >> 7)
-        tb[r + c * ld] = T[(d0 + r) + static_cast<long>(d0 + c) * ldt];
+      for (int c0 = threadIdx.x >> 7; c0 < bs; c0 += 16 * cstep) {
+        double v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int c = c0 + j * cstep;
+          v[j] = c < bs ? T[(d0 + r) + static_cast<long>(d0 + c) * ldt] : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+          if (c0 + j * cstep < bs) tb[r + (c0 + j * cstep) * ld] = v[j];
+      }
   }
   __syncthreads();
   if (threadIdx.x >= 32) return;
@@ -875,9 +908,193 @@ void trsv_attr() {
 }  // namespace emul
 
 namespace emul {
+
+namespace {
+
+constexpr int kSolveBs = 128;      // diagonal block of the persistent solve
+constexpr int kPermSmemMax = 54 * 1024;   // rows whose permutation fits in shared memory (4 B each, + 4 KB)
+
+// x <- P x for the interchanges ipiv[0..n) (1-based, applied in order): the
+// composite permutation is built by one thread in shared memory (ipiv staged in
+// chunks), then x is gathered through tmp.  One block.
+__global__ void __launch_bounds__(1024) permute_rhs_kernel(const int32_t* ipiv, int n, double* x, double* tmp) {
+  extern __shared__ int perm[];
+  __shared__ int chunk[1024];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) perm[i] = i;
+  __syncthreads();
+  for (int k0 = 0; k0 < n; k0 += 1024) {
+    const int m = n - k0 < 1024 ? n - k0 : 1024;
+    if (static_cast<int>(threadIdx.x) < m) chunk[threadIdx.x] = ipiv[k0 + threadIdx.x] - 1;
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int j = 0; j < m; ++j) {
+        const int k = k0 + j, p = chunk[j];
+        if (p != k && p >= 0 && p < n) {
+          const int t = perm[k];
+          perm[k] = perm[p];
+          perm[p] = t;
+        }
+      }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tmp[i] = x[perm[i]];
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = tmp[i];
+}
+
+// Bounded grid barrier on a monotonic arrival counter (zeroed before the
+// launch); returns false on timeout after recording it in *status.
+__device__ bool solve_sync(unsigned long long* cnt, unsigned long long target, long long limit, int* status) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    bool ok = true;
+    if (atomicAdd(cnt, 1ull) + 1 < target) {
+      volatile unsigned long long* vc = cnt;
+      const long long t0 = clock64();
+      while (*vc < target)
+        if (clock64() - t0 > limit) {
+          ok = false;
+          atomicExch(status, kStatusTimeout);
+          break;
+        }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// Forward (L unit lower) and back (U) substitution with the factors of
+// emul_dgetrf for one right-hand side, in one cooperative launch: for each
+// 128-row diagonal block, block 0 stages it and solves it in one warp (x in
+// registers, broadcast by shuffle, division by the diagonal of U), then every
+// block applies the block's column of L (or U) to its share of the remaining
+// rows.  Two bounded grid barriers per diagonal block.  A row's owner block
+// changes from step to step, so x is read and written through L2 only.
+__global__ void __launch_bounds__(256) getrs1_kernel(const double* LU, long lda, int n, double* x,
+                                                     unsigned long long* cnt, int* status, long long limit) {
+  extern __shared__ double tb[];   // kSolveBs x (kSolveBs + 1) staging of a diagonal block (block 0)
+  __shared__ double xs[kSolveBs];
+  constexpr int ld = kSolveBs + 1;
+  const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+  const int nblk = (n + kSolveBs - 1) / kSolveBs;
+  unsigned long long target = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool lower = pass == 0;
+    for (int s = 0; s < nblk; ++s) {
+      const int d = lower ? s : nblk - 1 - s;
+      const int d0 = d * kSolveBs, bs = n - d0 < kSolveBs ? n - d0 : kSolveBs;
+      if (b == 0) {
+        {
+          const int r = tid & 127, cstep = blockDim.x >> 7;
+          if (r < bs)
+            for (int c0 = tid >> 7; c0 < bs; c0 += 16 * cstep) {
+              double v[16];
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                const int c = c0 + j * cstep;
+                v[j] = c < bs ? __ldg(LU + (d0 + r) + static_cast<long>(d0 + c) * lda) : 0.0;
+              }
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                if (c0 + j * cstep < bs) tb[r + (c0 + j * cstep) * ld] = v[j];
+            }
+        }
+        __syncthreads();
+        if (tid < 32) {
+          double v[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) v[q] = lane + 32 * q < bs ? __ldcg(x + d0 + lane + 32 * q) : 0.0;
+          if (lower) {
+#pragma unroll
+            for (int q0 = 0; q0 < 4; ++q0)
+              for (int kk = 0; kk < 32; ++kk) {
+                const int k = 32 * q0 + kk;
+                if (k >= bs) break;
+                const double xk = __shfl_sync(0xFFFFFFFFu, v[q0], kk);
+#pragma unroll
+                for (int q = q0; q < 4; ++q) {
+                  const int i = lane + 32 * q;
+                  if (i > k && i < bs) v[q] = fma(-tb[i + k * ld], xk, v[q]);
+                }
+              }
+          } else {
+#pragma unroll
+            for (int q0 = 3; q0 >= 0; --q0)
+              for (int kk = 31; kk >= 0; --kk) {
+                const int k = 32 * q0 + kk;
+                if (k >= bs) continue;
+                if (lane == kk) v[q0] = v[q0] / tb[k + k * ld];
+                const double xk = __shfl_sync(0xFFFFFFFFu, v[q0], kk);
+#pragma unroll
+                for (int q = 0; q <= q0; ++q) {
+                  const int i = lane + 32 * q;
+                  if (i < k) v[q] = fma(-tb[i + k * ld], xk, v[q]);
+                }
+              }
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (lane + 32 * q < bs) __stcg(x + d0 + lane + 32 * q, v[q]);
+        }
+      }
+      target += G;
+      if (!solve_sync(cnt, target, limit, status)) return;
+      // rows below (forward) or above (backward) the block
+      const int r_lo = lower ? d0 + bs : 0, r_hi = lower ? n : d0;
+      if (r_hi > r_lo) {
+        for (int c = tid; c < bs; c += blockDim.x) xs[c] = __ldcg(x + d0 + c);
+        __syncthreads();
+        for (int r = r_lo + b * blockDim.x + tid; r < r_hi; r += G * blockDim.x) {
+          double acc = 0.0;
+          for (int c = 0; c < bs; ++c) acc = fma(__ldg(LU + r + static_cast<long>(d0 + c) * lda), xs[c], acc);
+          __stcg(x + r, __ldcg(x + r) - acc);
+        }
+      }
+      target += G;
+      if (!solve_sync(cnt, target, limit, status)) return;
+    }
+  }
+}
+
+}  // namespace
+
 // Solve with the factors of emul_dgetrf (arguments validated by the caller).
 int getrs_body(emul_handle_t h, int n, int nrhs, const double* LU, int lda, const int32_t* ipiv, double* B,
                int ldb) {
+  if (nrhs == 1 && n <= kPermSmemMax) {
+    // one right-hand side: permutation in one block, both substitutions in one cooperative launch
+    int rc = reserve_workspace(h, 2 * kAl + al(static_cast<size_t>(n) * 8));
+    if (rc) return rc;
+    uint8_t* ws = static_cast<uint8_t*>(h->ws);
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ws);
+    double* tmp = reinterpret_cast<double*>(ws + kAl);
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaFuncSetAttribute(permute_rhs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPermSmemMax * 4);
+      cudaFuncSetAttribute(getrs1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kSolveBs * (kSolveBs + 1) * 8);
+      attr_set = true;
+    }
+    permute_rhs_kernel<<<1, 1024, static_cast<size_t>(n) * 4, h->stream>>>(ipiv, n, B, tmp);
+    h->launches++;
+    rc = check_cuda(h, cudaGetLastError(), "rhs permutation");
+    if (rc) return rc;
+    rc = check_cuda(h, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), h->stream), "solve barrier");
+    if (rc) return rc;
+    long ldl = lda;
+    long long limit = h->wait_limit;
+    int* status = h->d_status;
+    void* args[] = {const_cast<double**>(&LU), &ldl, &n, &B, &cnt, &status, &limit};
+    h->launches++;
+    return check_cuda(h,
+                      cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(getrs1_kernel), dim3(h->nsm),
+                                                  dim3(256), args, kSolveBs * (kSolveBs + 1) * 8, h->stream),
+                      "solve");
+  }
   const size_t need = lu_extra_bytes(16, h->nsm);
   int rc = reserve_workspace(h, need);
   if (rc) return rc;
