@@ -806,7 +806,7 @@ LuBufs carve(emul_handle_t h, size_t off, int nb) {
 int launch_leaf(emul_handle_t h, double* A, long lda, int n, int d0, int w, int pc0, int pc1, int32_t* ipiv,
                 int32_t* info, const LuBufs& B) {
   const int mp = n - d0;
-  int G = (mp + 255) / 256;
+  int G = (mp + 127) / 128;   // 128 rows per block: the per-column FP64 work of a block overlaps the exchange
   const int smem_rows_cap = 200 * 1024 / (w * 8);
   if ((mp + G - 1) / G > smem_rows_cap) G = (mp + smem_rows_cap - 1) / smem_rows_cap;
   if (G < 1) G = 1;
