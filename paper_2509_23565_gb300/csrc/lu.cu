@@ -434,6 +434,37 @@ __global__ void __launch_bounds__(256) laswp_apply_kernel(double* A, long lda, i
   }
 }
 
+// Deferred interchanges of the L columns.  G is the composite gather of the
+// interchanges of all later panels (G[r]: the row whose content ends at row r)
+// and H its inverse; prepending a panel's interchanges (its gather map: row
+// dst[i] receives the original row src[i], a permutation of the touched rows)
+// changes only the rows r = H[dst[i]]: G[r] = src[i], H[src[i]] = r.
+__global__ void iota2_kernel(int n, int* G, int* H) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    G[i] = i;
+    H[i] = i;
+  }
+}
+
+__global__ void compose_kernel(const int* map, int* G, int* H) {
+  __shared__ int rr[2 * kPermMax];
+  const int cnt = map[4 * kPermMax];
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) rr[i] = H[map[i]];
+  __syncthreads();
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const int src = map[2 * kPermMax + i];
+    G[rr[i]] = src;
+    H[src] = rr[i];
+  }
+}
+
+// tmp[(r - r0) + c (n - r0)] = A[G[r], c0 + c] for r in [r0, n); blockIdx.y = c.
+__global__ void gather_rows_kernel(const double* A, long lda, int r0, int n, int c0, const int* G, double* tmp) {
+  const int r = r0 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (r < n) tmp[(r - r0) + static_cast<long>(c) * (n - r0)] = A[G[r] + static_cast<long>(c0 + c) * lda];
+}
+
 // X (w1 x w2 at A[d0.., c0..]) <- L^-1 X with L unit lower w1 x w1 at A[d0.., d0..]
 // (w1 <= 128).  The strictly lower part of L is staged in shared memory; one
 // warp per column of X (cpb columns per block), lane l holding rows l, l+32,
@@ -1146,7 +1177,9 @@ int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int n
   int rc = emul::check_cuda(h, cudaMemsetAsync(info, 0, sizeof(int32_t), h->stream), "info reset");
   if (rc) return rc;
   const size_t gw = emul::gemm_workspace_bytes(n, n, nb, s_fixed, false);
-  rc = emul::reserve_workspace(h, gw + emul::lu_extra_bytes(nb, h->nsm));
+  // after the product and LU buffers: G, H (n ints each) and one panel of rows (n x nb doubles)
+  const size_t def_off = emul::al(emul::al(gw) + emul::lu_extra_bytes(nb, h->nsm));
+  rc = emul::reserve_workspace(h, def_off + emul::al(8ull * n) + emul::al(8ull * n * nb));
   if (rc) return rc;
   const emul::LuBufs B = emul::carve(h, gw, nb);
   rc = emul::check_cuda(h, cudaMemsetAsync(B.recs, 0, emul::rec_bytes(h->nsm), h->stream), "leaf records");
@@ -1163,8 +1196,7 @@ int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int n
     ph = emul::phase_begin(h, EMUL_PHASE_SWAP);
     rc = emul::laswp_prepare(h, ipiv, j0, j0 + jb, B.map);
     if (rc) return rc;
-    rc = emul::laswp_apply(h, A, lda, 0, j0, B.map);
-    if (rc) return rc;
+    // the columns left of the panel get all later interchanges at once, after the loop
     rc = emul::laswp_apply(h, A, lda, j0 + jb, n, B.map);
     emul::phase_end(h, ph);
     if (rc) return rc;
@@ -1254,6 +1286,33 @@ int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int n
     if (stats) stats->steps++;
   }
   if (stats) stats->slices_mean = updates ? slices_sum / updates : static_cast<double>(s_fixed);
+  // the L columns of every panel but the last: all interchanges of the later
+  // panels, composed from the last panel back and gathered once per panel
+  const int K = (n + nb - 1) / nb;
+  if (K > 1) {
+    const int ph = emul::phase_begin(h, EMUL_PHASE_SWAP);
+    int* G = reinterpret_cast<int*>(static_cast<uint8_t*>(h->ws) + def_off);
+    int* H = G + n;
+    double* tmp = reinterpret_cast<double*>(static_cast<uint8_t*>(h->ws) + def_off + emul::al(8ull * n));
+    emul::iota2_kernel<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, h->stream>>>(n, G, H);
+    h->launches++;
+    for (int k = K - 2; k >= 0; --k) {
+      const int r0 = (k + 1) * nb, r1 = r0 + nb < n ? r0 + nb : n;
+      rc = emul::laswp_prepare(h, ipiv, r0, r1, B.map);
+      if (rc) return rc;
+      emul::compose_kernel<<<1, 512, 0, h->stream>>>(B.map, G, H);
+      emul::gather_rows_kernel<<<dim3((n - r0 + 255) / 256, nb), 256, 0, h->stream>>>(A, lda, r0, n, k * nb, G,
+                                                                                         tmp);
+      h->launches += 2;
+      rc = emul::check_cuda(h,
+                            cudaMemcpy2DAsync(A + r0 + static_cast<long>(k) * nb * lda, static_cast<size_t>(lda) * 8,
+                                              tmp, static_cast<size_t>(n - r0) * 8, static_cast<size_t>(n - r0) * 8,
+                                              nb, cudaMemcpyDeviceToDevice, h->stream),
+                            "deferred interchanges");
+      if (rc) return rc;
+    }
+    emul::phase_end(h, ph);
+  }
   return EMUL_OK;
 }
 
