@@ -999,95 +999,123 @@ __device__ bool solve_sync(unsigned long long* cnt, unsigned long long target, l
 }
 
 // Forward (L unit lower) and back (U) substitution with the factors of
-// emul_dgetrf for one right-hand side, in one cooperative launch: for each
-// 128-row diagonal block, block 0 stages it and solves it in one warp (x in
-// registers, broadcast by shuffle, division by the diagonal of U), then every
-// block applies the block's column of L (or U) to its share of the remaining
-// rows.  Two bounded grid barriers per diagonal block.  A row's owner block
-// changes from step to step, so x is read and written through L2 only.
+// emul_dgetrf for one right-hand side, in one cooperative launch.  Step s
+// (the 128-row diagonal blocks of L, then those of U from the bottom) is
+// solved by block s % G in one warp (x in registers, broadcast by shuffle,
+// multiplication by the reciprocals of U's diagonal, formed while staging);
+// block (s+1) % G stages the next diagonal block meanwhile.  Then every warp of
+// every block applies the block's column of L (or U) to 32-row groups of the
+// remaining rows.  Two bounded grid barriers per step.  A row's owner changes
+// from step to step, so x is read and written through L2 only.
+__device__ void solve_stage(const double* LU, long lda, int d0, int bs, bool lower, double* tb, double* rcp) {
+  constexpr int ld = kSolveBs + 1;
+  const int tid = threadIdx.x;
+  const int r = tid & 127, cstep = blockDim.x >> 7;
+  if (r < bs)
+    for (int c0 = tid >> 7; c0 < bs; c0 += 16 * cstep) {
+      double v[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int c = c0 + j * cstep;
+        v[j] = c < bs ? __ldg(LU + (d0 + r) + static_cast<long>(d0 + c) * lda) : 0.0;
+      }
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (c0 + j * cstep < bs) tb[r + (c0 + j * cstep) * ld] = v[j];
+    }
+  __syncthreads();
+  if (!lower && tid < bs) rcp[tid] = 1.0 / tb[tid + tid * ld];
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(256) getrs1_kernel(const double* LU, long lda, int n, double* x,
                                                      unsigned long long* cnt, int* status, long long limit) {
-  extern __shared__ double tb[];   // kSolveBs x (kSolveBs + 1) staging of a diagonal block (block 0)
+  extern __shared__ double tb[];   // kSolveBs x (kSolveBs + 1) staging of a diagonal block
   __shared__ double xs[kSolveBs];
+  __shared__ double rcp[kSolveBs];
   constexpr int ld = kSolveBs + 1;
-  const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+  const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nblk = (n + kSolveBs - 1) / kSolveBs;
+  const int nsteps = 2 * nblk;
+  auto info = [&](int st, bool& lower, int& d0, int& bs) {
+    lower = st < nblk;
+    const int d = lower ? st : 2 * nblk - 1 - st;
+    d0 = d * kSolveBs;
+    bs = n - d0 < kSolveBs ? n - d0 : kSolveBs;
+  };
   unsigned long long target = 0;
-  for (int pass = 0; pass < 2; ++pass) {
-    const bool lower = pass == 0;
-    for (int s = 0; s < nblk; ++s) {
-      const int d = lower ? s : nblk - 1 - s;
-      const int d0 = d * kSolveBs, bs = n - d0 < kSolveBs ? n - d0 : kSolveBs;
-      if (b == 0) {
-        {
-          const int r = tid & 127, cstep = blockDim.x >> 7;
-          if (r < bs)
-            for (int c0 = tid >> 7; c0 < bs; c0 += 16 * cstep) {
-              double v[16];
+  int staged = -1;   // step whose diagonal block this block holds in tb
+  for (int st = 0; st < nsteps; ++st) {
+    bool lower;
+    int d0, bs;
+    info(st, lower, d0, bs);
+    const int sb = st % G, nxt = (st + 1) % G;
+    if (b == sb) {
+      if (staged != st) solve_stage(LU, lda, d0, bs, lower, tb, rcp);
+      staged = -1;
+      if (tid < 32) {
+        double v[4];
 #pragma unroll
-              for (int j = 0; j < 16; ++j) {
-                const int c = c0 + j * cstep;
-                v[j] = c < bs ? __ldg(LU + (d0 + r) + static_cast<long>(d0 + c) * lda) : 0.0;
+        for (int q = 0; q < 4; ++q) v[q] = lane + 32 * q < bs ? __ldcg(x + d0 + lane + 32 * q) : 0.0;
+        if (lower) {
+#pragma unroll
+          for (int q0 = 0; q0 < 4; ++q0)
+            for (int kk = 0; kk < 32; ++kk) {
+              const int k = 32 * q0 + kk;
+              if (k >= bs) break;
+              const double xk = __shfl_sync(0xFFFFFFFFu, v[q0], kk);
+#pragma unroll
+              for (int q = q0; q < 4; ++q) {
+                const int i = lane + 32 * q;
+                if (i > k && i < bs) v[q] = fma(-tb[i + k * ld], xk, v[q]);
               }
+            }
+        } else {
 #pragma unroll
-              for (int j = 0; j < 16; ++j)
-                if (c0 + j * cstep < bs) tb[r + (c0 + j * cstep) * ld] = v[j];
+          for (int q0 = 3; q0 >= 0; --q0)
+            for (int kk = 31; kk >= 0; --kk) {
+              const int k = 32 * q0 + kk;
+              if (k >= bs) continue;
+              if (lane == kk) v[q0] = v[q0] * rcp[k];
+              const double xk = __shfl_sync(0xFFFFFFFFu, v[q0], kk);
+#pragma unroll
+              for (int q = 0; q <= q0; ++q) {
+                const int i = lane + 32 * q;
+                if (i < k) v[q] = fma(-tb[i + k * ld], xk, v[q]);
+              }
             }
         }
-        __syncthreads();
-        if (tid < 32) {
-          double v[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) v[q] = lane + 32 * q < bs ? __ldcg(x + d0 + lane + 32 * q) : 0.0;
-          if (lower) {
-#pragma unroll
-            for (int q0 = 0; q0 < 4; ++q0)
-              for (int kk = 0; kk < 32; ++kk) {
-                const int k = 32 * q0 + kk;
-                if (k >= bs) break;
-                const double xk = __shfl_sync(0xFFFFFFFFu, v[q0], kk);
-#pragma unroll
-                for (int q = q0; q < 4; ++q) {
-                  const int i = lane + 32 * q;
-                  if (i > k && i < bs) v[q] = fma(-tb[i + k * ld], xk, v[q]);
-                }
-              }
-          } else {
-#pragma unroll
-            for (int q0 = 3; q0 >= 0; --q0)
-              for (int kk = 31; kk >= 0; --kk) {
-                const int k = 32 * q0 + kk;
-                if (k >= bs) continue;
-                if (lane == kk) v[q0] = v[q0] / tb[k + k * ld];
-                const double xk = __shfl_sync(0xFFFFFFFFu, v[q0], kk);
-#pragma unroll
-                for (int q = 0; q <= q0; ++q) {
-                  const int i = lane + 32 * q;
-                  if (i < k) v[q] = fma(-tb[i + k * ld], xk, v[q]);
-                }
-              }
-          }
-#pragma unroll
-          for (int q = 0; q < 4; ++q)
-            if (lane + 32 * q < bs) __stcg(x + d0 + lane + 32 * q, v[q]);
-        }
+        for (int q = 0; q < 4; ++q)
+          if (lane + 32 * q < bs) __stcg(x + d0 + lane + 32 * q, v[q]);
       }
-      target += G;
-      if (!solve_sync(cnt, target, limit, status)) return;
-      // rows below (forward) or above (backward) the block
-      const int r_lo = lower ? d0 + bs : 0, r_hi = lower ? n : d0;
-      if (r_hi > r_lo) {
-        for (int c = tid; c < bs; c += blockDim.x) xs[c] = __ldcg(x + d0 + c);
-        __syncthreads();
-        for (int r = r_lo + b * blockDim.x + tid; r < r_hi; r += G * blockDim.x) {
+    } else if (b == nxt && st + 1 < nsteps) {
+      // the next step's solver stages its diagonal block while this one is solved
+      bool l2;
+      int e0, es;
+      info(st + 1, l2, e0, es);
+      solve_stage(LU, lda, e0, es, l2, tb, rcp);
+      staged = st + 1;
+    }
+    target += G;
+    if (!solve_sync(cnt, target, limit, status)) return;
+    // rows below (forward) or above (backward) the block, 32-row groups over all warps
+    const int r_lo = lower ? d0 + bs : 0, r_hi = lower ? n : d0;
+    if (r_hi > r_lo) {
+      for (int c = tid; c < bs; c += blockDim.x) xs[c] = __ldcg(x + d0 + c);
+      __syncthreads();
+      const int wpb = blockDim.x >> 5;
+      for (int rg = b * wpb + warp; r_lo + rg * 32 < r_hi; rg += G * wpb) {
+        const int r = r_lo + rg * 32 + lane;
+        if (r < r_hi) {
           double acc = 0.0;
           for (int c = 0; c < bs; ++c) acc = fma(__ldg(LU + r + static_cast<long>(d0 + c) * lda), xs[c], acc);
           __stcg(x + r, __ldcg(x + r) - acc);
         }
       }
-      target += G;
-      if (!solve_sync(cnt, target, limit, status)) return;
     }
+    target += G;
+    if (!solve_sync(cnt, target, limit, status)) return;
   }
 }
 
