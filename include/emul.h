@@ -63,6 +63,24 @@ int emul_sync_status(emul_handle_t handle);
 /* Bytes of device workspace currently held by the handle. */
 size_t emul_workspace_bytes(emul_handle_t handle);
 
+/* Host-only introspection of the product kernel's schedule (the order in
+ * which the level sums I_L of Sec. 2 are accumulated; the paper fixes only
+ * their values, not this order): the sweeps and the TMEM slot plan the kernel
+ * would use for `slices` slices and inner dimension k.  wide = 1 selects the
+ * 64-column variant, level_sums = 1 the emul_level_sums mode.  Needs no GPU.
+ *   sweeps     out, cap_sweeps rows of EMUL_SWEEP_INTS ints:
+ *              k0c, k1c (K chunks of 32), L[2], pb[2], pe[2], flags[2], rel[2],
+ *              nplanes, kcs (L[1] = 0: one job; flags: 1 open, 2 stash,
+ *              4 take, 8 final; rel: jobs from a stash to its take)
+ *   table      out, cap_table bytes: slot (bits 0-1) and barrier parity
+ *              (bit 2) of job j in tile phase ph at ph * njobs + j
+ *   meta       out, 5 ints: nsweeps, njobs, t0, period, table bytes
+ * Returns EMUL_OK, EMUL_INVALID_ARG (no schedule for these arguments, or a
+ * capacity too small; meta is still filled when a schedule exists). */
+#define EMUL_SWEEP_INTS 14
+int emul_schedule(int slices, int k, int wide, int level_sums, int* sweeps, int cap_sweeps, unsigned char* table,
+                  int cap_table, int* meta);
+
 /* ---------------------------------------------------------------- steps --
  * Exposed individually so each step of the method can be checked bit for bit.
  */

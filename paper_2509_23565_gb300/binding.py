@@ -29,6 +29,7 @@ SIGNATURES = {
     "emul_last_error": (ctypes.c_char_p, [_vp]),
     "emul_sync_status": (_c_int, [_vp]),
     "emul_workspace_bytes": (ctypes.c_size_t, [_vp]),
+    "emul_schedule": (_c_int, [_c_int, _c_int, _c_int, _c_int, _vp, _c_int, _vp, _c_int, _vp]),
     "emul_split": (_c_int, [_vp, _c_int, _c_int, _vp, _c_long, _c_long, _c_int, _vp, _vp, _c_long]),
     "emul_level_sums": (_c_int, [_vp, _c_int, _c_int, _c_int, _vp, _c_int, _vp, _c_int, _c_int, _vp, _c_int,
                                  _c_long]),
@@ -301,6 +302,30 @@ class Emul:
         self._check(self.lib.emul_backward_error(self.h, A.m, _vp(A.ptr), A.ld, _vp(x.ptr), _vp(b.ptr),
                                                  _vp(out.data_ptr())), "emul_backward_error")
         return out
+
+
+SWEEP_FIELDS = ("k0c", "k1c", "L0", "L1", "pb0", "pb1", "pe0", "pe1", "flags0", "flags1", "rel0", "rel1",
+                "nplanes", "kcs")
+
+
+def schedule(slices, k, wide=False, level_sums=False):
+    """Product-kernel schedule for (slices, k) from emul_schedule (host only):
+    (list of sweep dicts with SWEEP_FIELDS, slot table bytes, meta dict), or
+    None when no schedule exists."""
+    L = load()
+    meta = (ctypes.c_int * 5)()
+    rc = L.emul_schedule(slices, k, int(wide), int(level_sums), None, 0, None, 0, meta)
+    if meta[0] == 0:
+        return None
+    sw = (ctypes.c_int * (meta[0] * len(SWEEP_FIELDS)))()
+    tab = (ctypes.c_ubyte * max(1, meta[4]))()
+    rc = L.emul_schedule(slices, k, int(wide), int(level_sums), sw, meta[0], tab, meta[4], meta)
+    if rc != 0:
+        raise EmulError(f"emul_schedule failed ({rc})")
+    n = len(SWEEP_FIELDS)
+    sweeps = [dict(zip(SWEEP_FIELDS, sw[i * n:(i + 1) * n])) for i in range(meta[0])]
+    info = {"nsweeps": meta[0], "njobs": meta[1], "t0": meta[2], "period": meta[3], "table_bytes": meta[4]}
+    return sweeps, bytes(tab[:meta[4]]), info
 
 
 def lib():

@@ -653,6 +653,32 @@ int emul_profile_read(emul_handle_t h, emul_profile* out) {
   return EMUL_OK;
 }
 
+int emul_schedule(int slices, int k, int wide, int level_sums, int* sweeps, int cap_sweeps, unsigned char* table,
+                  int cap_table, int* meta) {
+  using namespace emul;
+  if (slices < 1 || slices > kMaxSlices || k < 1 || !meta) return EMUL_INVALID_ARG;
+  const int nch = (k + kBK - 1) / kBK;
+  std::vector<Sweep> v;
+  std::vector<uint8_t> tab;
+  int njobs = 0, t0 = 0, period = 0;
+  if (!build_schedule(slices, nch, wide != 0, level_sums != 0, v, tab, njobs, t0, period)) return EMUL_INVALID_ARG;
+  meta[0] = static_cast<int>(v.size());
+  meta[1] = njobs;
+  meta[2] = t0;
+  meta[3] = period;
+  meta[4] = static_cast<int>(tab.size());
+  if (!sweeps || !table || cap_sweeps < static_cast<int>(v.size()) || cap_table < static_cast<int>(tab.size()))
+    return EMUL_INVALID_ARG;
+  for (size_t i = 0; i < v.size(); ++i) {
+    const Sweep& w = v[i];
+    const int row[EMUL_SWEEP_INTS] = {w.k0c,      w.k1c,      w.L[0],     w.L[1],   w.pb[0],   w.pb[1],  w.pe[0],
+                                      w.pe[1],    w.flags[0], w.flags[1], w.rel[0], w.rel[1], w.nplanes, w.kcs};
+    for (int j = 0; j < EMUL_SWEEP_INTS; ++j) sweeps[i * EMUL_SWEEP_INTS + j] = row[j];
+  }
+  std::memcpy(table, tab.data(), tab.size());
+  return EMUL_OK;
+}
+
 int emul_split(emul_handle_t h, int rows, int k, const double* X, long rs, long cs, int slices, int32_t* exps,
                uint16_t* slice_out, long ldk) {
   if (!h) return EMUL_INVALID_ARG;

@@ -1,0 +1,193 @@
+"""Host-side checks of the product kernel's schedule and TMEM slot plan
+(emul_schedule; no GPU needed).
+
+The level sums I_L = sum_{p+q=L} S_p^A S_q^B of Sec. 2 are accumulated in
+jobs (one level, a pair range, a K range) grouped into sweeps; the epilogue
+folds them by Horner's rule, T = sum_L I_L 2^(7(t-L)).  Checked here for every
+slice count and a range of k, both variants and both modes:
+* every slice pair (p, q) with p + q <= t = s + 1 and every K chunk is summed
+  exactly once, and no job exceeds the exact-accumulation budget
+  (k_job * pairs <= 1040, so |I| < 2^24 in FP32);
+* the job flags implement Horner's rule: each level's contributions end with
+  weight 2^(7(t-L)) (a missing or extra shift fails);
+* a sweep stages every plane its pairs use, within the stage's s planes;
+* the slot table drives the MMA/epilogue barrier protocol without deadlock,
+  with the parity bit of each job equal to the parity of its slot's use count
+  (simulated independently of the planner, from the barrier semantics).
+"""
+import pytest
+
+from paper_2509_23565_gb300 import binding
+
+BUDGET = 1040
+KBK = 32
+OPEN, STASH, TAKE, FINAL = 1, 2, 4, 8
+KS = (1, 16, 32, 33, 64, 100, 128, 200, 224, 256, 300, 512, 1000, 2048)
+
+
+def jobs_of(sweeps):
+    out = []
+    for si, w in enumerate(sweeps):
+        for j in (0, 1):
+            if w[f"L{j}"] == 0:
+                continue
+            out.append({"sweep": si, "L": w[f"L{j}"], "pb": w[f"pb{j}"], "pe": w[f"pe{j}"], "c0": w["k0c"],
+                        "c1": w["k1c"], "flags": w[f"flags{j}"], "rel": w[f"rel{j}"]})
+    return out
+
+
+def get(s, k, wide, ls):
+    r = binding.schedule(s, k, wide=wide, level_sums=ls)
+    if wide:
+        assert r is not None, f"the wide variant must schedule any k (s={s}, k={k})"
+    return r
+
+
+@pytest.mark.parametrize("s", range(1, 9))
+def test_coverage_budget_planes(s):
+    for k in KS:
+        for wide in (False, True):
+            r = get(s, k, wide, False)
+            if r is None:
+                continue
+            sweeps, _, _ = r
+            nch = (k + KBK - 1) // KBK
+            t = s + 1
+            count = {}
+            for w in sweeps:
+                assert 0 <= w["k0c"] < w["k1c"] <= nch
+                assert w["kcs"] >= 1 and w["kcs"] * w["nplanes"] <= s and w["nplanes"] <= s
+                for j in (0, 1):
+                    L = w[f"L{j}"]
+                    if L == 0:
+                        continue
+                    pb, pe = w[f"pb{j}"], w[f"pe{j}"]
+                    assert 1 <= pb <= pe and 2 <= L <= t
+                    assert (pe - pb + 1) * (w["k1c"] - w["k0c"]) * KBK <= BUDGET
+                    for p in range(pb, pe + 1):
+                        q = L - p
+                        assert 1 <= q <= s
+                        assert max(p, q) <= w["nplanes"]
+                        for c in range(w["k0c"], w["k1c"]):
+                            count[(p, q, c)] = count.get((p, q, c), 0) + 1
+            want = {(p, q, c) for p in range(1, s + 1) for q in range(1, s + 1) if p + q <= t
+                    for c in range(nch)}
+            assert set(count) == want, (s, k, wide)
+            assert all(v == 1 for v in count.values()), (s, k, wide)
+
+
+@pytest.mark.parametrize("s", range(1, 9))
+def test_horner_flags(s):
+    """Symbolic epilogue: R holds (level, weight exponent) terms; OPEN shifts by 7,
+    a job adds its level at exponent 0, a stash is added at its take, FINAL is
+    R * 2^7 + I.  Every level must end at exponent 7 (t - L)."""
+    t = s + 1
+    for k in KS:
+        for wide in (False, True):
+            r = get(s, k, wide, False)
+            if r is None:
+                continue
+            jobs = jobs_of(r[0])
+            R = []          # list of [level, exponent, weight in pairs*chunks]
+            stash = None
+            finals = 0
+            for jb in jobs:
+                amount = (jb["pe"] - jb["pb"] + 1) * (jb["c1"] - jb["c0"])
+                if jb["flags"] & STASH:
+                    assert stash is None
+                    stash = (jb["L"], amount)
+                    continue
+                add = [(jb["L"], amount)]
+                if jb["flags"] & TAKE:
+                    assert stash is not None and stash[0] == jb["L"]
+                    add.append(stash)
+                    stash = None
+                if jb["flags"] & (OPEN | FINAL):
+                    for term in R:
+                        term[1] += 7
+                for L, a in add:
+                    R.append([L, 0, a])
+                if jb["flags"] & FINAL:
+                    finals += 1
+                    assert jb is jobs[-1]
+            assert stash is None
+            assert finals == (0 if wide else 1), (s, k, wide)
+            nch = (k + KBK - 1) // KBK
+            per_level = {}
+            for L, e, a in R:
+                assert e == 7 * (t - L), (s, k, wide, L, e)
+                per_level[L] = per_level.get(L, 0) + a
+            for L in range(2, t + 1):
+                pairs = sum(1 for p in range(1, s + 1) if 1 <= L - p <= s)
+                assert per_level.get(L, 0) == pairs * nch
+
+
+@pytest.mark.parametrize("s", range(1, 9))
+def test_slot_protocol(s):
+    """Barrier-level simulation over several tiles: the MMA side takes a sweep
+    when every slot it needs has been released as often as it was allocated;
+    the epilogue drains jobs in order (a stash waits for its take and is
+    released with it).  The table's parity bit must equal the slot's use count
+    parity; the simulation must run to the end (no deadlock)."""
+    for k in KS:
+        for wide in (False, True):
+            for ls in (False, True):
+                r = get(s, k, wide, ls)
+                if r is None:
+                    continue
+                sweeps, tab, info = r
+                nj, t0, per = info["njobs"], info["t0"], info["period"]
+                jobs = jobs_of(sweeps)
+                assert len(jobs) == nj and per >= 1
+                ntiles = t0 + 2 * per + 1
+                alloc = [0, 0, 0, 0]
+                rel = [0, 0, 0, 0]
+                full = {}            # (tile, job) -> slot, once the MMA has committed it
+                mma = (0, 0)         # (tile, sweep)
+                epi = (0, 0)         # (tile, job)
+                stash = None
+                steps = 0
+                while epi[0] < ntiles:
+                    steps += 1
+                    assert steps < 100000
+                    progressed = False
+                    if mma[0] < ntiles:
+                        tile, si = mma
+                        ph = tile if tile < t0 else t0 + (tile - t0) % per
+                        idx = [j for j, jb in enumerate(jobs) if jb["sweep"] == si]
+                        slots = [tab[ph * nj + j] & 3 for j in idx]
+                        assert len(set(slots)) == len(slots)
+                        if all(rel[sl] == alloc[sl] for sl in slots):
+                            for j, sl in zip(idx, slots):
+                                assert (tab[ph * nj + j] >> 2) & 1 == alloc[sl] & 1, (s, k, wide, ls)
+                                alloc[sl] += 1
+                                full[(tile, j)] = sl
+                            mma = (tile, si + 1) if si + 1 < len(sweeps) else (tile + 1, 0)
+                            progressed = True
+                    tile, j = epi
+                    if (tile, j) in full:
+                        jb = jobs[j]
+                        sl = full[(tile, j)]
+                        if not ls and jb["flags"] & STASH:
+                            stash = sl
+                        else:
+                            rel[sl] += 1
+                            if not ls and jb["flags"] & TAKE:
+                                assert stash is not None
+                                rel[stash] += 1
+                                stash = None
+                        epi = (tile, j + 1) if j + 1 < nj else (tile + 1, 0)
+                        progressed = True
+                    assert progressed, f"deadlock s={s} k={k} wide={wide} level_sums={ls} at {mma} {epi}"
+
+
+def test_lu_schedule_shape():
+    """The LU's trailing update (s = 7, k = nb = 256, narrow) uses the banded
+    schedule: levels {2}, {3,4}, {5,6} and {7,8} in K halves, 16 staged planes
+    per K chunk."""
+    sweeps, _, info = binding.schedule(7, 256)
+    levels = [(w["L0"], w["L1"]) for w in sweeps]
+    assert levels == [(2, 0), (3, 4), (5, 6), (5, 6), (7, 8), (7, 8)]
+    nch = 8
+    assert sum(w["nplanes"] * (w["k1c"] - w["k0c"]) for w in sweeps) == 16 * nch
+    assert info["njobs"] == 11
