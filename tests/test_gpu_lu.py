@@ -184,3 +184,27 @@ def test_getrf_large_backward_error(gpu_lib, n):
     gpu_lib.dgetrs(dA, ipiv, db)
     x = db.numpy()[:, 0]
     assert residual.backward_error(A, x, b) < 16
+
+
+def test_profile_phases(gpu_lib):
+    """With profiling on, every phase of a factorization with more than one
+    panel, and the solve, report device time (CUDA events)."""
+    import torch
+    n, nb = 1200, 128
+    A = inputs.uniform(n, n, seed=91)
+    b = inputs.vector(n, seed=92)
+    gpu_lib.profile_read()
+    gpu_lib.profile_enable(True)
+    try:
+        dA, ipiv, info = _factor(gpu_lib, A, nb, 7)
+        x = ColMajor.from_numpy(b.reshape(n, 1))
+        gpu_lib.dgetrs(dA, ipiv, x)
+        torch.cuda.synchronize()
+        prof = gpu_lib.profile_read()
+    finally:
+        gpu_lib.profile_enable(False)
+    assert info == 0
+    ph = prof["phase_ms"]
+    for name in ("panel", "swap", "u12", "update", "solve"):
+        assert ph[name] > 0.0, (name, ph)
+    assert prof["product_launches"] > 0 and prof["kernel_launches"] > 0
