@@ -16,6 +16,9 @@
 // with one slice set serving both operands.
 #include <cmath>
 #include <cstdio>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include <cuda_runtime.h>
 
@@ -795,6 +798,17 @@ __global__ void probe_check_kernel(int m, int n, int k, const double* L, long ld
 }
 
 // ------------------------------------------------------------------ host helpers
+// Raise a kernel's dynamic shared-memory limit once per device: the attribute
+// belongs to the device, and one process may drive several GPUs.
+void smem_attr(const void* fn, int bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.insert({dev, fn}).second) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
 struct LuBufs {
   double* inv;          // nb x nb
   uint64_t* recs;       // leaf pivot exchange: [2][nsm][kRecWords] epoch-tagged words
@@ -846,11 +860,7 @@ int launch_leaf(emul_handle_t h, double* A, long lda, int n, int d0, int w, int 
   const int R = (mp + G - 1) / G;
   const size_t smem = static_cast<size_t>(R) * w * 8;
   if (smem > 220 * 1024) return set_error(h, EMUL_NOT_SUPPORTED, "panel too tall for the leaf kernel");
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(getf2_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-    attr_set = true;
-  }
+  smem_attr(reinterpret_cast<const void*>(getf2_leaf_kernel), 220 * 1024);
   long long limit = h->wait_limit;
   int* status = h->d_status;
   // epochs of this launch: (salt << 5) | column, salt > 0 and new per launch
@@ -893,11 +903,7 @@ int laswp(emul_handle_t h, double* A, long lda, int c0, int c1, const int32_t* i
 int trsm_small(emul_handle_t h, double* A, long lda, int d0, int w1, int c0, int w2) {
   if (w1 <= 0 || w2 <= 0) return EMUL_OK;
   if (w1 > kTrsmMax) return set_error(h, EMUL_NOT_SUPPORTED, "panel trsm wider than 128");
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(trsm_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmMax * kTrsmMax * 8);
-    attr_set = true;
-  }
+  smem_attr(reinterpret_cast<const void*>(trsm_small_kernel), kTrsmMax * kTrsmMax * 8);
   // one column per block: the solve is FP64-bound (about 1.6 FMA per clock per
   // SM), so it is spread over as many SMs as columns; 256 threads stage L
   trsm_small_kernel<<<w2, 256, static_cast<size_t>(w1) * w1 * 8, h->stream>>>(A, lda, d0, w1, c0, w2, 1);
@@ -928,13 +934,7 @@ int rgetrf(emul_handle_t h, double* A, long lda, int n, int d0, int w, int pc0, 
 
 }  // namespace
 
-void trsv_attr() {
-  static bool done = false;
-  if (!done) {
-    cudaFuncSetAttribute(trsv_block_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 129 * 8);
-    done = true;
-  }
-}
+void trsv_attr() { smem_attr(reinterpret_cast<const void*>(trsv_block_kernel), 128 * 129 * 8); }
 
 }  // namespace emul
 
@@ -1131,13 +1131,8 @@ int getrs_body(emul_handle_t h, int n, int nrhs, const double* LU, int lda, cons
     uint8_t* ws = static_cast<uint8_t*>(h->ws);
     unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ws);
     double* tmp = reinterpret_cast<double*>(ws + kAl);
-    static bool attr_set = false;
-    if (!attr_set) {
-      cudaFuncSetAttribute(permute_rhs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPermSmemMax * 4);
-      cudaFuncSetAttribute(getrs1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           kSolveBs * (kSolveBs + 1) * 8);
-      attr_set = true;
-    }
+    smem_attr(reinterpret_cast<const void*>(permute_rhs_kernel), kPermSmemMax * 4);
+    smem_attr(reinterpret_cast<const void*>(getrs1_kernel), kSolveBs * (kSolveBs + 1) * 8);
     permute_rhs_kernel<<<1, 1024, static_cast<size_t>(n) * 4, h->stream>>>(ipiv, n, B, tmp);
     h->launches++;
     rc = check_cuda(h, cudaGetLastError(), "rhs permutation");
