@@ -348,7 +348,7 @@ def run_gemm(args):
 
 
 def run_selector(args):
-    """Ablation of the learned slice selector (BASELINE config 4): LU + solve with
+    """Ablation of the learned slice selector (mixed dynamic ranges): LU + solve with
     slices chosen per step by the trained network (plus the a-posteriori probe)
     against fixed s = 8, on a uniform and on a mixed-range matrix."""
     import torch
@@ -390,7 +390,7 @@ def run_selector(args):
 
 
 def run_batched(args):
-    """BASELINE config 5: many uneven LU solves (n log-uniform in [64, 1024],
+    """Many uneven LU solves (n log-uniform in [64, 1024],
     uniform(-1,1) entries, half of them scaled with r = 8) in one persistent,
     graph-recorded launch: reduced-slice factorization + FP64 refinement."""
     import torch
@@ -408,8 +408,8 @@ def run_batched(args):
         b0.append(v)
         bs.append(ColMajor(v.clone().view(1, int(n)), int(n), 1))
     lib = Emul()
-    tune_path = os.path.join(ROOT, "gpurun_out", "batched_autotune.json") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else None
+    cache_dir = os.path.join(ROOT, "paper_2509_23565_gb300", "_build")   # build products, not tracked
+    tune_path = os.path.join(cache_dir, "batched_autotune.json") if os.path.isdir(cache_dir) else None
     t0 = time.perf_counter()
     lib.autotune(tune_path)
     t_tune = time.perf_counter() - t0

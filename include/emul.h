@@ -160,7 +160,7 @@ int emul_backward_error(emul_handle_t h, int n, const double* A, int lda, const 
 
 /* ------------------------------------------------------ batched solves --
  * Many independent systems A_i x_i = b_i of uneven sizes (1..4096) in one
- * persistent launch recorded in a CUDA graph (BASELINE config 5): each block
+ * persistent launch recorded in a CUDA graph: each block
  * takes whole systems from a work queue (largest first) and factors them in
  * reduced precision -- FP32 panel with partial pivoting, trailing updates by
  * the split-integer product (Sec. 2, Eq. 2) with `slices` INT8 slices as exact
@@ -192,7 +192,7 @@ int emul_autotune(emul_handle_t h, const char* cache_path);
 
 /* ------------------------------------------------------ slice selector --
  * A small MLP predicts, per trailing update, the fewest slices that keep the
- * update within FP64 accuracy (BASELINE config 4; the paper's Sec. 3 cites
+ * update within FP64 accuracy (the paper's Sec. 3 cites
  * a-posteriori validation of error-free products, which the check below
  * follows).  Features (64 floats): 32-bin histograms of each entry's exponent
  * offset from its row scale (A) and from its column scale (B), each divided

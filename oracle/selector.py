@@ -1,4 +1,4 @@
-"""Oracle of the learned slice selector (BASELINE config 4; the a-posteriori
+"""Oracle of the learned slice selector (slice count per product block; the a-posteriori
 check follows the validated error-free products the paper cites in Sec. 3).
 
 * features(A, B): 32-bin histograms of the exponent offset of every entry from

@@ -1,5 +1,5 @@
 // Batched solves of many independent, uneven systems A_i x_i = b_i in one
-// persistent launch (BASELINE config 5), with the split-integer product of
+// persistent launch, with the split-integer product of
 // arXiv 2509.23565 (Sec. 2, Eq. 2) at a reduced slice count in the LU
 // factorization and FP64 iterative refinement on the residual of Eq. 8.
 //

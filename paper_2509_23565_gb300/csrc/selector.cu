@@ -1,4 +1,4 @@
-// Learned slice selector and its training data (BASELINE config 4; the
+// Learned slice selector and its training data (the
 // a-posteriori check follows the validated error-free products cited in
 // Sec. 3 of arXiv 2509.23565).
 //

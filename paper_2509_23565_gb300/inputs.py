@@ -107,7 +107,7 @@ def log_scaled_device(m, n, r, gen, device="cuda"):
 def mixed_range(n, nb, ranges, seed):
     """Uniform(-1, 1) matrix whose block rows (nb rows each) are scaled
     entrywise by 10**e, e ~ U(-r, r), with r drawn per block row from `ranges`
-    (BASELINE config 4: mixed blocks r in {0, 8, 16})."""
+    (mixed blocks, e.g. r in {0, 8, 16})."""
     rng = _rng(seed)
     A = rng.random((n, n)) * 2.0 - 1.0
     for i0 in range(0, n, nb):

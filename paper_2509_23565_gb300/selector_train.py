@@ -1,4 +1,4 @@
-"""Training driver of the slice selector (BASELINE config 4).
+"""Training driver of the slice selector (slice count per product block).
 
 Tuples (features, label) are generated by the method itself on the GPU: for a
 random product block drawn from the dynamic-range generators (u 10^e, e in
