@@ -347,6 +347,42 @@ def run_gemm(args):
                                    "frac": ach / peak, "peak_kind": f"bf16 dense burst, {kind}"}}), flush=True)
 
 
+def run_table2(args):
+    """The paper's scaling table of ParaWilk parameters (alpha = 1): for each n,
+    the (d, b) it found to push the scaled residual (Eq. 8) above 16 with 6 and
+    with 7 splits, and our residual for those parameters (one draw of the
+    random fill, nb = 64), next to the printed value.  Reported, not asserted."""
+    import torch
+    from paper_2509_23565_gb300 import inputs
+    from paper_2509_23565_gb300.binding import ColMajor, Emul
+    lib = Emul()
+    rows = []
+    with open(os.path.join(ROOT, "tests", "golden", "table2_parawilk.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                rows.append([float(v) for v in line.split()])
+    out = []
+    t0 = time.perf_counter()
+    for n, d6, b6, r6, d7, b7, r7 in rows:
+        n = int(n)
+        bvec = inputs.vector(n, seed=n + 1)
+        entry = {"n": n}
+        for s, d, bb, want in ((6, d6, b6, r6), (7, d7, b7, r7)):
+            A = inputs.parawilk_random(n, int(d), int(bb), 1.0, seed=n)
+            A0 = torch.from_numpy(np.ascontiguousarray(A.T)).cuda()
+            W = ColMajor(A0.clone(), n, n)
+            x = ColMajor(torch.from_numpy(bvec.copy()).cuda().view(1, n), n, 1)
+            ipiv, info = lib.dgetrf(W, nb=64, slices=s)
+            lib.dgetrs(W, ipiv, x)
+            be = lib.backward_error(ColMajor(A0, n, n), x, ColMajor(torch.from_numpy(bvec).cuda().view(1, n), n, 1))
+            entry[f"s{s}"] = {"d": int(d), "b": int(bb), "scaled_residual": float(be.cpu().numpy()[0]),
+                              "paper": want}
+        out.append(entry)
+    print(json.dumps({"metric": "scaled residual (Eq. 8) at the paper's ParaWilk parameters, 6 and 7 splits",
+                      "config": {"workload": "ParaWilk_n(d, b, 1) with random fill, n = 256..2048, nb = 64"},
+                      "seconds": time.perf_counter() - t0, "rows": out}), flush=True)
+
+
 def run_selector(args):
     """Ablation of the learned slice selector (mixed dynamic ranges): LU + solve with
     slices chosen per step by the trained network (plus the a-posteriori probe)
@@ -447,7 +483,7 @@ def main():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="lu", choices=["lu", "gemm", "selector", "batched"])
+    p.add_argument("--workload", default="lu", choices=["lu", "gemm", "selector", "batched", "table2"])
     p.add_argument("--batch-count", type=int, default=4096)
     p.add_argument("--k", type=int, default=256)
     p.add_argument("--n", type=int, default=32768)
@@ -474,6 +510,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args)
+        return
+    if args.workload == "table2":
+        run_table2(args)
         return
     world, rank, local = dist_setup()
     run_ours(args, world, rank, local)
