@@ -67,7 +67,8 @@ size_t emul_workspace_bytes(emul_handle_t handle);
  * which the level sums I_L of Sec. 2 are accumulated; the paper fixes only
  * their values, not this order): the sweeps and the TMEM slot plan the kernel
  * would use for `slices` slices and inner dimension k.  wide = 1 selects the
- * 64-column variant, level_sums = 1 the emul_level_sums mode.  Needs no GPU.
+ * 64-column variant, level_sums = 1 the emul_level_sums mode; threshold is
+ * the last level kept (0: slices + 1; else 2..2*slices).  Needs no GPU.
  *   sweeps     out, cap_sweeps rows of EMUL_SWEEP_INTS ints:
  *              k0c, k1c (K chunks of 32), L[2], pb[2], pe[2], flags[2], rel[2],
  *              nplanes, kcs (L[1] = 0: one job; flags: 1 open, 2 stash,
@@ -78,8 +79,8 @@ size_t emul_workspace_bytes(emul_handle_t handle);
  * Returns EMUL_OK, EMUL_INVALID_ARG (no schedule for these arguments, or a
  * capacity too small; meta is still filled when a schedule exists). */
 #define EMUL_SWEEP_INTS 14
-int emul_schedule(int slices, int k, int wide, int level_sums, int* sweeps, int cap_sweeps, unsigned char* table,
-                  int cap_table, int* meta);
+int emul_schedule(int slices, int k, int wide, int level_sums, int threshold, int* sweeps, int cap_sweeps,
+                  unsigned char* table, int cap_table, int* meta);
 
 /* ---------------------------------------------------------------- steps --
  * Exposed individually so each step of the method can be checked bit for bit.
@@ -114,6 +115,17 @@ int emul_level_sums(emul_handle_t h, int m, int n, int k, const double* A, int l
  */
 int emul_dgemm(emul_handle_t h, int m, int n, int k, double alpha, const double* A, int lda, const double* B,
                int ldb, double beta, double* C, int ldc, int slices);
+
+/* emul_dgemm with the truncation threshold as a parameter (Section 2, Eq. 2:
+ * the slice pairs kept are those with p + q <= t).  threshold = 0 is the
+ * method's t = s + 1 (identical to emul_dgemm); 2 <= threshold <= 2s keeps the
+ * levels L = 2..threshold, threshold = 2s being the full s^2-pair product.
+ * The result is D = RN(sum_{L<=t} I_L 2^(e + f - 7L)), exact sum, one rounding.
+ * Returns EMUL_INVALID_ARG for a threshold outside that range and
+ * EMUL_NOT_SUPPORTED when k is too large for the 128-bit Horner state at this
+ * threshold (sum_L n_L 127^2 2^(7(t-L)) k >= 2^126). */
+int emul_dgemm_threshold(emul_handle_t h, int m, int n, int k, double alpha, const double* A, int lda,
+                         const double* B, int ldb, double beta, double* C, int ldc, int slices, int threshold);
 
 /* ------------------------------------------------------- factorizations --
  * Optional statistics of a factorization call (host memory, may be NULL).

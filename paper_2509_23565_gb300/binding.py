@@ -29,12 +29,14 @@ SIGNATURES = {
     "emul_last_error": (ctypes.c_char_p, [_vp]),
     "emul_sync_status": (_c_int, [_vp]),
     "emul_workspace_bytes": (ctypes.c_size_t, [_vp]),
-    "emul_schedule": (_c_int, [_c_int, _c_int, _c_int, _c_int, _vp, _c_int, _vp, _c_int, _vp]),
+    "emul_schedule": (_c_int, [_c_int, _c_int, _c_int, _c_int, _c_int, _vp, _c_int, _vp, _c_int, _vp]),
     "emul_split": (_c_int, [_vp, _c_int, _c_int, _vp, _c_long, _c_long, _c_int, _vp, _vp, _c_long]),
     "emul_level_sums": (_c_int, [_vp, _c_int, _c_int, _c_int, _vp, _c_int, _vp, _c_int, _c_int, _vp, _c_int,
                                  _c_long]),
     "emul_dgemm": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_double, _vp, _c_int, _vp, _c_int, _c_double, _vp,
                             _c_int, _c_int]),
+    "emul_dgemm_threshold": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_double, _vp, _c_int, _vp, _c_int, _c_double,
+                                      _vp, _c_int, _c_int, _c_int]),
     "emul_dgetrf": (_c_int, [_vp, _c_int, _vp, _c_int, _vp, _c_int, _c_int, _vp, _vp]),
     "emul_dgetrs": (_c_int, [_vp, _c_int, _c_int, _vp, _c_int, _vp, _vp, _c_int]),
     "emul_dpotrf": (_c_int, [_vp, _c_char, _c_int, _vp, _c_int, _c_int, _c_int, _vp, _vp]),
@@ -193,9 +195,14 @@ class Emul:
         return out   # out[L-2, j, i] = I_L(i, j)
 
     # ---------------------------------------------------------------- BLAS / LAPACK
-    def dgemm(self, A, B, C, slices, alpha=1.0, beta=0.0):
-        self._check(self.lib.emul_dgemm(self.h, C.m, C.n, A.n, alpha, _vp(A.ptr), A.ld, _vp(B.ptr), B.ld, beta,
-                                        _vp(C.ptr), C.ld, slices), "emul_dgemm")
+    def dgemm(self, A, B, C, slices, alpha=1.0, beta=0.0, t=None):
+        if t is None:
+            self._check(self.lib.emul_dgemm(self.h, C.m, C.n, A.n, alpha, _vp(A.ptr), A.ld, _vp(B.ptr), B.ld, beta,
+                                            _vp(C.ptr), C.ld, slices), "emul_dgemm")
+        else:
+            self._check(self.lib.emul_dgemm_threshold(self.h, C.m, C.n, A.n, alpha, _vp(A.ptr), A.ld, _vp(B.ptr),
+                                                      B.ld, beta, _vp(C.ptr), C.ld, slices, t),
+                        "emul_dgemm_threshold")
 
     def dgetrf(self, A, nb=0, slices=7, stats=False):
         import torch
@@ -308,18 +315,19 @@ SWEEP_FIELDS = ("k0c", "k1c", "L0", "L1", "pb0", "pb1", "pe0", "pe1", "flags0", 
                 "nplanes", "kcs")
 
 
-def schedule(slices, k, wide=False, level_sums=False):
-    """Product-kernel schedule for (slices, k) from emul_schedule (host only):
-    (list of sweep dicts with SWEEP_FIELDS, slot table bytes, meta dict), or
-    None when no schedule exists."""
+def schedule(slices, k, wide=False, level_sums=False, t=0):
+    """Product-kernel schedule for (slices, k) and levels 2..t (t = 0:
+    slices + 1) from emul_schedule (host only): (list of sweep dicts with
+    SWEEP_FIELDS, slot table bytes, meta dict), or None when no schedule
+    exists."""
     L = load()
     meta = (ctypes.c_int * 5)()
-    rc = L.emul_schedule(slices, k, int(wide), int(level_sums), None, 0, None, 0, meta)
+    rc = L.emul_schedule(slices, k, int(wide), int(level_sums), t, None, 0, None, 0, meta)
     if meta[0] == 0:
         return None
     sw = (ctypes.c_int * (meta[0] * len(SWEEP_FIELDS)))()
     tab = (ctypes.c_ubyte * max(1, meta[4]))()
-    rc = L.emul_schedule(slices, k, int(wide), int(level_sums), sw, meta[0], tab, meta[4], meta)
+    rc = L.emul_schedule(slices, k, int(wide), int(level_sums), t, sw, meta[0], tab, meta[4], meta)
     if rc != 0:
         raise EmulError(f"emul_schedule failed ({rc})")
     n = len(SWEEP_FIELDS)

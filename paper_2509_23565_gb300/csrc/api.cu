@@ -19,12 +19,13 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 inline long kpad_of(int k) { return (static_cast<long>(k) + 7) / 8 * 8; }
 
-// Sum over the levels L = 2..t-1 of n_L 2^(7(t-1-L)) times 127^2, the worst-case
-// magnitude per unit of k of the Horner state before the last level.
-long double horner_bound_per_k(int s) {
-  const int t = s + 1;
+// Sum over the levels L = 2..last of n_L 2^(7(last-L)) times 127^2: the
+// worst-case magnitude per unit of k of the Horner state after level `last`
+// (t - 1 for the narrow variant's state before its final level, t for the
+// wide variant's complete state).
+long double horner_bound_per_k(int s, int last) {
   long double acc = 0.0L;
-  for (int L = 2; L <= t - 1; ++L) {
+  for (int L = 2; L <= last; ++L) {
     int nL = 0;
     for (int p = 1; p <= s; ++p)
       if (L - p >= 1 && L - p <= s) ++nL;
@@ -81,9 +82,8 @@ void push_sweep(std::vector<Sweep>& out, const Job& a, const Job* b) {
 // the pair does not fit the exactness budget over the whole K it runs as two
 // K halves, the first half of L+1 stashed until L is complete.  The bands
 // minimise the staged planes per K chunk (dynamic programme over the levels).
-bool build_banded(int s, int nch, bool wide, std::vector<Sweep>& out) {
+bool build_banded(int s, int t, int nch, bool wide, std::vector<Sweep>& out) {
   out.clear();
-  const int t = s + 1;
   const int kInf = 1 << 28;
   std::vector<int> cost(t + 3, 0), choice(t + 3, 0);
   auto groups = [&](int seg) { return (nch + seg - 1) / seg; };
@@ -145,9 +145,8 @@ bool build_banded(int s, int nch, bool wide, std::vector<Sweep>& out) {
 // fit, or (wide variant) its K range into segments.  Consecutive jobs of one K
 // range share a sweep.  In the narrow variant the last level's jobs (at most
 // two) form the final sweep.
-bool build_levelwise(int s, int nch, bool wide, std::vector<Sweep>& out) {
+bool build_levelwise(int s, int t, int nch, bool wide, std::vector<Sweep>& out) {
   out.clear();
-  const int t = s + 1;
   std::vector<Job> jobs, held;
   const int kc = nch * kBK;
   for (int L = 2; L <= t; ++L) {
@@ -245,8 +244,6 @@ bool plan_slots(const std::vector<Sweep>& sw, bool mode1, std::vector<uint8_t>& 
   return false;
 }
 
-// Schedule and slot plan: the banded schedule when it exists and plans, else
-// the level-ordered one.
 // K chunks per stage: a stage holds s tiles of A and s of B, so a sweep that
 // stages fewer planes packs several chunks into one stage (one barrier phase
 // for more bytes; the copy engine's rate grows with the bytes per phase).
@@ -259,10 +256,15 @@ void set_chunks_per_stage(int s, std::vector<Sweep>& out) {
   }
 }
 
+// Schedule and slot plan for the levels 2..t (t = 0: the default threshold
+// s + 1 of the method): the banded schedule when it exists and plans, else the
+// level-ordered one.
 bool build_schedule(int s, int nch, bool wide, bool mode1, std::vector<Sweep>& out, std::vector<uint8_t>& tab,
-                    int& njobs, int& t0, int& period) {
-  if (!(build_banded(s, nch, wide, out) && plan_slots(out, mode1, tab, njobs, t0, period)) &&
-      !(build_levelwise(s, nch, wide, out) && plan_slots(out, mode1, tab, njobs, t0, period)))
+                    int& njobs, int& t0, int& period, int t = 0) {
+  if (t == 0) t = s + 1;
+  if (t < 2 || t > 2 * s) return false;
+  if (!(build_banded(s, t, nch, wide, out) && plan_slots(out, mode1, tab, njobs, t0, period)) &&
+      !(build_levelwise(s, t, nch, wide, out) && plan_slots(out, mode1, tab, njobs, t0, period)))
     return false;
   set_chunks_per_stage(s, out);
   return true;
@@ -271,23 +273,32 @@ bool build_schedule(int s, int nch, bool wide, bool mode1, std::vector<Sweep>& o
 // The narrow variant keeps the Horner state in int64 and rounds T = R 2^7 + I
 // on a 64-bit magnitude (a 128-bit path covers |R| >= 2^57): it needs the last
 // level in at most two jobs and |R| well inside int64.
-bool narrow_ok(int s, int k) {
+bool narrow_ok(int s, int k, int t = 0) {
+  if (t == 0) t = s + 1;
   if (s > 7) return false;
   const int nch = (k + kBK - 1) / kBK;
   std::vector<Sweep> tmp;
   std::vector<uint8_t> tab;
   int nj, t0, per;
-  if (!build_schedule(s, nch, false, false, tmp, tab, nj, t0, per)) return false;
-  const long double bound = horner_bound_per_k(s) * static_cast<long double>(nch * kBK);
+  if (!build_schedule(s, nch, false, false, tmp, tab, nj, t0, per, t)) return false;
+  const long double bound = horner_bound_per_k(s, t - 1) * static_cast<long double>(nch * kBK);
   return bound < 4.0e18L;   // < 2^62
+}
+
+// The wide variant's complete 128-bit Horner state must stay below 2^126.
+bool wide_ok(int s, int t, int k) {
+  const int nch = (k + kBK - 1) / kBK;
+  return horner_bound_per_k(s, t) * static_cast<long double>(nch * kBK) < 8.5e37L;
 }
 
 // Device copy of a schedule: the sweeps, then the slot table (16-byte aligned).
 size_t schedule_bytes(size_t nsweeps, size_t ntab) { return nsweeps * sizeof(Sweep) + 16 + ntab; }
 
-int get_schedule(emul_handle_t h, int s, int nch, bool wide, bool mode1, Sweep** dptr, int* count, SlotPlan* plan) {
+int get_schedule(emul_handle_t h, int s, int t, int nch, bool wide, bool mode1, Sweep** dptr, int* count,
+                 SlotPlan* plan) {
   const uint32_t key = (static_cast<uint32_t>(s) << 24) | (static_cast<uint32_t>(wide) << 23) |
-                       (static_cast<uint32_t>(mode1) << 22) | static_cast<uint32_t>(nch);
+                       (static_cast<uint32_t>(mode1) << 22) | (static_cast<uint32_t>(t) << 13) |
+                       static_cast<uint32_t>(nch);   // nch < 2^13 (k <= 65536)
   auto it = h->sched_cache.find(key);
   if (it != h->sched_cache.end()) {
     *dptr = it->second.sched;
@@ -298,7 +309,7 @@ int get_schedule(emul_handle_t h, int s, int nch, bool wide, bool mode1, Sweep**
   std::vector<Sweep> v;
   std::vector<uint8_t> tab;
   SlotPlan sp{};
-  if (!build_schedule(s, nch, wide, mode1, v, tab, sp.njobs, sp.t0, sp.period))
+  if (!build_schedule(s, nch, wide, mode1, v, tab, sp.njobs, sp.t0, sp.period, t))
     return set_error(h, EMUL_INVALID_ARG, "no schedule for this slice count / k");
   const size_t off_tab = (v.size() * sizeof(Sweep) + 15) / 16 * 16;
   std::vector<uint8_t> blob(off_tab + tab.size(), 0);
@@ -391,7 +402,9 @@ size_t gemm_workspace_bytes(int m, int n, int k, int s, bool same_operand) {
 }
 
 int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Operand B, double beta, double* C,
-             long ldc, int s, bool lower, int mode, int32_t* levels, long ldl, long ldl_plane, size_t ws_offset) {
+             long ldc, int s, bool lower, int mode, int32_t* levels, long ldl, long ldl_plane, size_t ws_offset,
+             int t) {
+  if (t == 0) t = s + 1;
   if (m <= 0 || n <= 0) return EMUL_OK;
   if (k <= 0) {
     if (mode == 1) {
@@ -434,12 +447,14 @@ int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Oper
     rc = check_cuda(h, cudaGetLastError(), "zero levels");
     if (rc) return rc;
   }
-  const bool wide = !narrow_ok(s, k);
+  const bool wide = !narrow_ok(s, k, t);
+  if (wide && mode == 0 && !wide_ok(s, t, k))
+    return set_error(h, EMUL_NOT_SUPPORTED, "threshold too high for this k: the 128-bit Horner state could overflow");
   const int nch = (k + kBK - 1) / kBK;
   Sweep* sched = nullptr;
   int nsweeps = 0;
   SlotPlan plan{};
-  rc = get_schedule(h, s, nch, wide, mode == 1, &sched, &nsweeps, &plan);
+  rc = get_schedule(h, s, t, nch, wide, mode == 1, &sched, &nsweeps, &plan);
   if (rc) return rc;
   const int BN = wide ? 64 : 128;
   CUtensorMap tmA, tmB;
@@ -453,7 +468,7 @@ int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Oper
   a.N = n;
   a.K = k;
   a.s = s;
-  a.t = s + 1;
+  a.t = t;
   a.alpha = alpha;
   a.beta = beta;
   a.C = C;
@@ -653,15 +668,17 @@ int emul_profile_read(emul_handle_t h, emul_profile* out) {
   return EMUL_OK;
 }
 
-int emul_schedule(int slices, int k, int wide, int level_sums, int* sweeps, int cap_sweeps, unsigned char* table,
-                  int cap_table, int* meta) {
+int emul_schedule(int slices, int k, int wide, int level_sums, int threshold, int* sweeps, int cap_sweeps,
+                  unsigned char* table, int cap_table, int* meta) {
   using namespace emul;
   if (slices < 1 || slices > kMaxSlices || k < 1 || !meta) return EMUL_INVALID_ARG;
+  if (threshold != 0 && (threshold < 2 || threshold > 2 * slices)) return EMUL_INVALID_ARG;
   const int nch = (k + kBK - 1) / kBK;
   std::vector<Sweep> v;
   std::vector<uint8_t> tab;
   int njobs = 0, t0 = 0, period = 0;
-  if (!build_schedule(slices, nch, wide != 0, level_sums != 0, v, tab, njobs, t0, period)) return EMUL_INVALID_ARG;
+  if (!build_schedule(slices, nch, wide != 0, level_sums != 0, v, tab, njobs, t0, period, threshold))
+    return EMUL_INVALID_ARG;
   meta[0] = static_cast<int>(v.size());
   meta[1] = njobs;
   meta[2] = t0;
@@ -701,15 +718,21 @@ int emul_level_sums(emul_handle_t h, int m, int n, int k, const double* A, int l
                         levels, ldl, ldl_plane);
 }
 
-int emul_dgemm(emul_handle_t h, int m, int n, int k, double alpha, const double* A, int lda, const double* B,
-               int ldb, double beta, double* C, int ldc, int slices) {
+int emul_dgemm_threshold(emul_handle_t h, int m, int n, int k, double alpha, const double* A, int lda,
+                         const double* B, int ldb, double beta, double* C, int ldc, int slices, int threshold) {
   if (!h) return EMUL_INVALID_ARG;
   if (m < 0 || n < 0 || k < 0 || slices < 1 || slices > emul::kMaxSlices || lda < (m > 1 ? m : 1) ||
       ldb < (k > 1 ? k : 1) || ldc < (m > 1 ? m : 1) || (m > 0 && n > 0 && !C) ||
-      (m > 0 && n > 0 && k > 0 && (!A || !B)) || k > 16384 * 4)
+      (m > 0 && n > 0 && k > 0 && (!A || !B)) || k > 16384 * 4 ||
+      (threshold != 0 && (threshold < 2 || threshold > 2 * slices)))
     return emul::set_error(h, EMUL_INVALID_ARG, "emul_dgemm: invalid argument");
   return emul::gemm_run(h, m, n, k, alpha, Operand{A, 1, lda}, Operand{B, ldb, 1}, beta, C, ldc, slices, false, 0,
-                        nullptr, 0, 0);
+                        nullptr, 0, 0, 0, threshold);
+}
+
+int emul_dgemm(emul_handle_t h, int m, int n, int k, double alpha, const double* A, int lda, const double* B,
+               int ldb, double beta, double* C, int ldc, int slices) {
+  return emul_dgemm_threshold(h, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, slices, 0);
 }
 
 }  // extern "C"

@@ -73,7 +73,8 @@ size_t gemm_workspace_bytes(int m, int n, int k, int s, bool same_operand);
 // `ws_offset` places the slices inside the workspace (callers running several
 // products back to back on one stream may share offset 0).
 int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Operand B, double beta, double* C,
-             long ldc, int s, bool lower, int mode, int32_t* levels, long ldl, long ldl_plane, size_t ws_offset = 0);
+             long ldc, int s, bool lower, int mode, int32_t* levels, long ldl, long ldl_plane, size_t ws_offset = 0,
+             int t = 0);   // t: truncation threshold, 0 = s + 1
 
 // Learned slice selector (selector.cu).
 int selector_features(emul_handle_t h, int m, int n, int k, Operand A, Operand B, float* feat);

@@ -119,3 +119,24 @@ def test_k_zero_and_beta_zero():
     assert (out == C).all()
     out = emulgemm.emul_gemm(A, B, 7)
     assert (out == 0).all()
+
+
+@pytest.mark.parametrize("s", [2, 3, 4])
+def test_threshold_full_product_correctly_rounded(s):
+    """Threshold t = 2s keeps every slice pair: with entries of at most 7s
+    significant bits below their row's (column's) scale nothing is truncated by
+    the split, so D_ij = RN(sum_k a_ik b_kj).  The method's t = s + 1 drops
+    the pairs with p + q > s + 1, which are nonzero here, and must differ."""
+    rng = np.random.default_rng(70 + s)
+    bits = 7 * s - 1
+    A = np.ldexp(rng.integers(-(2**bits), 2**bits, (6, 30)).astype(np.float64), -bits)
+    B = np.ldexp(rng.integers(-(2**bits), 2**bits, (30, 5)).astype(np.float64), -bits)
+    A[:, 0] = 0.5 + 2.0**-bits       # row scales 2^0
+    B[0, :] = -(0.5 + 2.0**-bits)    # column scales 2^0
+    ex = exact.exact_product(A, B)
+    want = np.array([[float(ex[i][j]) for j in range(5)] for i in range(6)])   # Fraction -> nearest double
+    assert np.array_equal(emulgemm.emul_gemm(A, B, s, t=2 * s), want)
+    assert not np.array_equal(emulgemm.emul_gemm(A, B, s), want)
+    # every intermediate threshold lies between: error non-increasing in t
+    errs = [float(np.max(np.abs(emulgemm.emul_gemm(A, B, s, t=t) - want))) for t in range(2, 2 * s + 1)]
+    assert all(a >= b for a, b in zip(errs, errs[1:])) and errs[-1] == 0.0, errs

@@ -5,8 +5,9 @@ The level sums I_L = sum_{p+q=L} S_p^A S_q^B of Sec. 2 are accumulated in
 jobs (one level, a pair range, a K range) grouped into sweeps; the epilogue
 folds them by Horner's rule, T = sum_L I_L 2^(7(t-L)).  Checked here for every
 slice count and a range of k, both variants and both modes:
-* every slice pair (p, q) with p + q <= t = s + 1 and every K chunk is summed
-  exactly once, and no job exceeds the exact-accumulation budget
+* every slice pair (p, q) with p + q <= t and every K chunk is summed
+  exactly once (t = s + 1, the method's threshold, and other thresholds
+  2 <= t <= 2s down to the full s^2-pair product), and no job exceeds the exact-accumulation budget
   (k_job * pairs <= 1040, so |I| < 2^24 in FP32);
 * the job flags implement Horner's rule: each level's contributions end with
   weight 2^(7(t-L)) (a missing or extra shift fails);
@@ -25,6 +26,13 @@ OPEN, STASH, TAKE, FINAL = 1, 2, 4, 8
 KS = (1, 16, 32, 33, 64, 100, 128, 200, 224, 256, 300, 512, 1000, 2048)
 
 
+def thresholds(s):
+    return sorted({t for t in (s + 1, 2, s, s + 2, 2 * s - 1, 2 * s) if 2 <= t <= 2 * s})
+
+
+ST = [(s, t) for s in range(1, 9) for t in thresholds(s)]
+
+
 def jobs_of(sweeps):
     out = []
     for si, w in enumerate(sweeps):
@@ -36,23 +44,22 @@ def jobs_of(sweeps):
     return out
 
 
-def get(s, k, wide, ls):
-    r = binding.schedule(s, k, wide=wide, level_sums=ls)
+def get(s, k, wide, ls, t):
+    r = binding.schedule(s, k, wide=wide, level_sums=ls, t=t)
     if wide:
         assert r is not None, f"the wide variant must schedule any k (s={s}, k={k})"
     return r
 
 
-@pytest.mark.parametrize("s", range(1, 9))
-def test_coverage_budget_planes(s):
+@pytest.mark.parametrize("s,t", ST)
+def test_coverage_budget_planes(s, t):
     for k in KS:
         for wide in (False, True):
-            r = get(s, k, wide, False)
+            r = get(s, k, wide, False, t)
             if r is None:
                 continue
             sweeps, _, _ = r
             nch = (k + KBK - 1) // KBK
-            t = s + 1
             count = {}
             for w in sweeps:
                 assert 0 <= w["k0c"] < w["k1c"] <= nch
@@ -76,15 +83,14 @@ def test_coverage_budget_planes(s):
             assert all(v == 1 for v in count.values()), (s, k, wide)
 
 
-@pytest.mark.parametrize("s", range(1, 9))
-def test_horner_flags(s):
+@pytest.mark.parametrize("s,t", ST)
+def test_horner_flags(s, t):
     """Symbolic epilogue: R holds (level, weight exponent) terms; OPEN shifts by 7,
     a job adds its level at exponent 0, a stash is added at its take, FINAL is
     R * 2^7 + I.  Every level must end at exponent 7 (t - L)."""
-    t = s + 1
     for k in KS:
         for wide in (False, True):
-            r = get(s, k, wide, False)
+            r = get(s, k, wide, False, t)
             if r is None:
                 continue
             jobs = jobs_of(r[0])
@@ -122,8 +128,8 @@ def test_horner_flags(s):
                 assert per_level.get(L, 0) == pairs * nch
 
 
-@pytest.mark.parametrize("s", range(1, 9))
-def test_slot_protocol(s):
+@pytest.mark.parametrize("s,t", ST)
+def test_slot_protocol(s, t):
     """Barrier-level simulation over several tiles: the MMA side takes a sweep
     when every slot it needs has been released as often as it was allocated;
     the epilogue drains jobs in order (a stash waits for its take and is
@@ -132,7 +138,7 @@ def test_slot_protocol(s):
     for k in KS:
         for wide in (False, True):
             for ls in (False, True):
-                r = get(s, k, wide, ls)
+                r = get(s, k, wide, ls, t)
                 if r is None:
                     continue
                 sweeps, tab, info = r
@@ -191,3 +197,11 @@ def test_lu_schedule_shape():
     nch = 8
     assert sum(w["nplanes"] * (w["k1c"] - w["k0c"]) for w in sweeps) == 16 * nch
     assert info["njobs"] == 11
+
+
+@pytest.mark.parametrize("s", [1, 4, 7])
+def test_threshold_out_of_range(s):
+    for t in (1, 2 * s + 1):
+        assert binding.schedule(s, 256, wide=True, t=t) is None
+    full = binding.schedule(s, 64, wide=True, t=2 * s)
+    assert full is not None and max(max(w["L0"], w["L1"]) for w in full[0]) == 2 * s
