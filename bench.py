@@ -7,6 +7,10 @@ updates with s INT8 slices) plus the solve (emul_dgetrs).  The TFLOP/s
 numerator is the HPL count 2/3 n^3 + 3/2 n^2.  The backward error
 ||Ax-b|| / (||A|| ||x|| n eps) of the last solve must stay <= 16.
 
+--workload lu_nopiv times the Level-3-only LU without pivoting of Section 6
+(emul_dgetrf_nopiv, block size --nb up to 4096) on a diagonally dominant
+matrix, with the same solve, checks and JSON keys.
+
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle (the
 project's plain reference of the same method) on a bounded sample.
 Multi-GPU (torchrun): replicas only; every rank factors its own matrix.
@@ -25,6 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "emulated-FP64 LU TFLOP/s vs native-FP64 LU on one GB300 at backward error ≤16"
+METRIC_NOPIV = "emulated-FP64 LU without pivoting TFLOP/s on one GB300 at backward error ≤16"
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum (673.4 + 516.2 MB) over the algorithmic
@@ -128,14 +133,18 @@ def aggregate_value(world, n, steps, ms_max):
     return world * lu_flops(n) * steps / (ms_max / 1e3) / 1e12
 
 
-def cpu_oracle_lu(n, nb, s, seed):
+def cpu_oracle_lu(n, nb, s, seed, nopiv=False):
     """Time the oracle's emulated LU + solve of one n x n matrix (bounded sample)."""
     from oracle import lu as olu, residual
     from paper_2509_23565_gb300 import inputs
-    A = inputs.uniform(n, n, seed=seed)
+    A = inputs.diag_dominant(n, seed=seed) if nopiv else inputs.uniform(n, n, seed=seed)
     b = inputs.vector(n, seed=seed + 1)
     t0 = time.perf_counter()
-    LU, piv, _ = olu.getrf(A, nb=nb, update="emulated", s=s)
+    if nopiv:
+        LU, _ = olu.getrf_nopiv(A, nb=nb, update="emulated", s=s)
+        piv = np.arange(1, n + 1)
+    else:
+        LU, piv, _ = olu.getrf(A, nb=nb, update="emulated", s=s)
     x = olu.getrs(LU, piv, b)
     dt = time.perf_counter() - t0
     return dt, residual.backward_error(A, x, b)
@@ -176,8 +185,10 @@ def run_ours(args, world, rank, local):
 
     torch.cuda.set_device(local)
     n, nb, s = args.n, args.nb, args.slices
+    nopiv = args.workload == "lu_nopiv"
     seed = 7000 + rank
-    A_host = inputs.uniform(n, n, seed=seed)                 # Fortran order
+    # Fortran order; the no-pivot LU needs a matrix that elimination without pivoting keeps stable
+    A_host = inputs.diag_dominant(n, seed=seed) if nopiv else inputs.uniform(n, n, seed=seed)
     b_host = inputs.vector(n, seed=seed + 1)
     A0 = torch.from_numpy(np.ascontiguousarray(A_host.T)).cuda()   # store (n, n): column-major A
     b0 = torch.from_numpy(b_host).cuda()
@@ -186,10 +197,12 @@ def run_ours(args, world, rank, local):
     lib = Emul()
     stream = torch.cuda.current_stream()
 
+    factor = lib.dgetrf_nopiv if nopiv else lib.dgetrf
+
     def step():
         work.store.copy_(A0)
         xb.store[0].copy_(b0)
-        ipiv, info = lib.dgetrf(work, nb=nb, slices=s)
+        ipiv, info = factor(work, nb=nb, slices=s)
         lib.dgetrs(work, ipiv, xb)
         return ipiv, info
 
@@ -245,11 +258,14 @@ def run_ours(args, world, rank, local):
                 "avg_launch_ms": prof["product_ms"] / max(1, prof["product_launches"]),
                 "share_of_step": prof["product_ms"] / ms}
 
+    workload = (f"LU without pivoting + solve, n={n} nb={nb} s={s}, A iid uniform(-1,1) with n on the diagonal, "
+                f"b uniform(-1,1)" if nopiv else
+                f"LU partial pivoting + solve, n={n} nb={nb} s={s}, A and b iid uniform(-1,1)")
     result = {
-        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "metric": METRIC_NOPIV if nopiv else METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"LU partial pivoting + solve, n={n} nb={nb} s={s}, A and b iid uniform(-1,1)",
+        "config": {"workload": workload,
                    "n": n, "nb": nb, "slices": s, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs (8 n^2 bytes) larger than L2; each step restores A from a device copy"},
         "backward_error": float(berr[1]), "scaled_residual_eq8": float(berr[0]), "info": info_v,
@@ -269,7 +285,7 @@ def run_ours(args, world, rank, local):
         for _ in range(args.e2e_steps):
             work.store.copy_(A_pin, non_blocking=True)
             xb.store[0].copy_(b_pin, non_blocking=True)
-            ipiv, info = lib.dgetrf(work, nb=nb, slices=s)
+            ipiv, info = factor(work, nb=nb, slices=s)
             lib.dgetrs(work, ipiv, xb)
             x_pin.copy_(xb.store[0], non_blocking=True)
         e1.record(stream)
@@ -287,7 +303,7 @@ def run_ours(args, world, rank, local):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        LU, piv = torch.linalg.lu_factor(Am)
+        LU, piv = torch.linalg.lu_factor(Am, pivot=not nopiv)
         x = torch.linalg.lu_solve(LU, piv, b0.view(n, 1))
         e1.record(stream)
         torch.cuda.synchronize()
@@ -295,15 +311,17 @@ def run_ours(args, world, rank, local):
         xn = ColMajor(x.t().contiguous(), n, 1)
         nb_err = lib.backward_error(A_chk, xn, b_chk).cpu().numpy()
         result["native_fp64"] = {"value": lu_flops(n) / (nms / 1e3) / 1e12, "unit": "TFLOP/s", "ms": nms,
-                                 "backward_error": float(nb_err[1]), "impl": "torch.linalg.lu_factor/lu_solve"}
+                                 "backward_error": float(nb_err[1]),
+                                 "impl": "torch.linalg.lu_factor/lu_solve" + (" (pivot=False)" if nopiv else "")}
         result["speedup_vs_native"] = result["native_fp64"]["ms"] / result["ms_per_step"]
         del LU, piv, x
 
     if rank == 0 and not args.no_cpu:
-        dt, cberr = cpu_oracle_lu(args.cpu_n, 64, s, 1234)
+        dt, cberr = cpu_oracle_lu(args.cpu_n, 64, s, 1234, nopiv)
         result["cpu_baseline"] = {"value": lu_flops(args.cpu_n) / dt / 1e12, "unit": "TFLOP/s",
                                   "cores": os.cpu_count(), "kind": "oracle",
-                                  "sample": f"oracle emulated LU + solve of one n={args.cpu_n} matrix (nb=64, "
+                                  "sample": f"oracle emulated {'no-pivot ' if nopiv else ''}LU + solve of one "
+                                            f"n={args.cpu_n} matrix (nb=64, "
                                             f"s={s}; numpy BLAS threads, exact recombination single-threaded)",
                                   "seconds": dt}
     if rank == 0:
@@ -483,11 +501,11 @@ def main():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="lu", choices=["lu", "gemm", "selector", "batched", "table2"])
+    p.add_argument("--workload", default="lu", choices=["lu", "lu_nopiv", "gemm", "selector", "batched", "table2"])
     p.add_argument("--batch-count", type=int, default=4096)
     p.add_argument("--k", type=int, default=256)
     p.add_argument("--n", type=int, default=32768)
-    p.add_argument("--nb", type=int, default=256)
+    p.add_argument("--nb", type=int, default=0, help="block size (0: 256 for lu, 1024 for lu_nopiv)")
     p.add_argument("--slices", type=int, default=7)
     p.add_argument("--cpu-n", type=int, default=512)
     p.add_argument("--e2e-steps", type=int, default=1)
@@ -495,6 +513,8 @@ def main():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     args = p.parse_args()
+    if args.nb == 0:
+        args.nb = 1024 if args.workload == "lu_nopiv" else 256
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

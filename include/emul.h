@@ -147,6 +147,22 @@ typedef struct emul_stats {
 int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int nb, int slices, int32_t* info,
                 emul_stats* stats);
 
+/* LU without pivoting of the n x n matrix A (lda), in place, A = L U (L unit
+ * lower, U upper): the Level-3-only factorization timed for blocking factors
+ * 256 to 2048 (Section 6), right-looking with block size nb (16..4096; 0 =
+ * 1024).  Every third-order step runs through the emulated product with
+ * `slices` slices: the Schur update A22 <- A22 - L21 U12 (Eq. 7), and the
+ * triangular solves through explicit inverses of the diagonal blocks (a
+ * panel is halved recursively down to blocks of at most 128 columns, factored
+ * in FP64).  No rows are exchanged, so the result is only as stable as
+ * Gaussian elimination without pivoting on A (diagonally dominant or SPD
+ * matrices need none).  A zero pivot sets *info to its 1-based index (the
+ * first one) and leaves its column unscaled; the later entries are then not
+ * meaningful.  info: 1 int32 (device).  emul_dgetrs solves with these factors
+ * given ipiv[i] = i + 1. */
+int emul_dgetrf_nopiv(emul_handle_t h, int n, double* A, int lda, int nb, int slices, int32_t* info,
+                      emul_stats* stats);
+
 /* Solve A X = B with the factors from emul_dgetrf: B (n x nrhs, ldb) is
  * overwritten by X.  FP64 substitution. */
 int emul_dgetrs(emul_handle_t h, int n, int nrhs, const double* LU, int lda, const int32_t* ipiv, double* B,

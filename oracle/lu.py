@@ -81,6 +81,40 @@ def getrf(A, nb=64, update="fp64", s=7):
     return A, ipiv, info[0]
 
 
+def getf2_nopiv(P, info_state, offset):
+    """Unblocked LU without pivoting of the panel P (m x b), in place; a zero
+    pivot leaves its column unscaled and sets info_state[0] (the first one)."""
+    m, b = P.shape
+    for j in range(min(m, b)):
+        if P[j, j] != 0.0:
+            P[j + 1:, j] = P[j + 1:, j] / P[j, j]
+        elif info_state[0] == 0:
+            info_state[0] = offset + j + 1
+        if j + 1 < b:
+            P[j + 1:, j + 1:] -= np.outer(P[j + 1:, j], P[j, j + 1:])
+
+
+def getrf_nopiv(A, nb=64, update="fp64", s=7):
+    """Right-looking blocked LU without pivoting, the Level-3-only variant of
+    Section 6: panel by unblocked elimination, U12 = L11^{-1} A12, then the
+    Schur complement of Eq. 7.  Returns (LU, info)."""
+    A = np.array(A, dtype=np.float64, order="F", copy=True)
+    n = A.shape[0]
+    assert A.shape == (n, n)
+    info = [0]
+    for j0 in range(0, n, nb):
+        jb = min(nb, n - j0)
+        getf2_nopiv(A[j0:, j0:j0 + jb], info, j0)
+        if j0 + jb < n:
+            L11 = A[j0:j0 + jb, j0:j0 + jb]
+            A[j0:j0 + jb, j0 + jb:] = solve_triangular(L11, A[j0:j0 + jb, j0 + jb:],
+                                                       lower=True, unit_diagonal=True)
+            L21 = A[j0 + jb:, j0:j0 + jb]
+            U12 = A[j0:j0 + jb, j0 + jb:]
+            A[j0 + jb:, j0 + jb:] = _trailing_update(L21, U12, A[j0 + jb:, j0 + jb:], update, s)
+    return A, info[0]
+
+
 def getrs(LU, ipiv, b):
     """Solve A x = b from getrf's output (row interchanges, then L, then U)."""
     LU = np.asarray(LU, dtype=np.float64)

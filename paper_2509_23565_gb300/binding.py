@@ -38,6 +38,7 @@ SIGNATURES = {
     "emul_dgemm_threshold": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_double, _vp, _c_int, _vp, _c_int, _c_double,
                                       _vp, _c_int, _c_int, _c_int]),
     "emul_dgetrf": (_c_int, [_vp, _c_int, _vp, _c_int, _vp, _c_int, _c_int, _vp, _vp]),
+    "emul_dgetrf_nopiv": (_c_int, [_vp, _c_int, _vp, _c_int, _c_int, _c_int, _vp, _vp]),
     "emul_dgetrs": (_c_int, [_vp, _c_int, _c_int, _vp, _c_int, _vp, _vp, _c_int]),
     "emul_dpotrf": (_c_int, [_vp, _c_char, _c_int, _vp, _c_int, _c_int, _c_int, _vp, _vp]),
     "emul_dpotrs": (_c_int, [_vp, _c_char, _c_int, _c_int, _vp, _c_int, _vp, _c_int]),
@@ -212,6 +213,16 @@ class Emul:
         self._check(self.lib.emul_dgetrf(self.h, A.m, _vp(A.ptr), A.ld, _vp(ipiv.data_ptr()), nb, slices,
                                          _vp(info.data_ptr()), ctypes.byref(st)), "emul_dgetrf")
         return (ipiv[:A.m], info, st) if stats else (ipiv[:A.m], info)
+
+    def dgetrf_nopiv(self, A, nb=0, slices=7, stats=False):
+        """LU without pivoting; returns (ipiv = 1..n for dgetrs, info[, stats])."""
+        import torch
+        info = torch.zeros(1, dtype=torch.int32, device="cuda")
+        st = Stats()
+        self._check(self.lib.emul_dgetrf_nopiv(self.h, A.m, _vp(A.ptr), A.ld, nb, slices, _vp(info.data_ptr()),
+                                               ctypes.byref(st)), "emul_dgetrf_nopiv")
+        ipiv = torch.arange(1, A.m + 1, dtype=torch.int32, device="cuda")
+        return (ipiv, info, st) if stats else (ipiv, info)
 
     def dgetrs(self, LU, ipiv, B):
         self._check(self.lib.emul_dgetrs(self.h, LU.m, B.n, _vp(LU.ptr), LU.ld, _vp(ipiv.data_ptr()), _vp(B.ptr),

@@ -6,6 +6,8 @@
 #include <vector>
 
 #include <mutex>
+#include <set>
+#include <utility>
 
 #include <cudaTypedefs.h>
 
@@ -366,6 +368,16 @@ __global__ void zero_levels_kernel(int m, int n, int planes, int32_t* lv, long l
 }
 
 }  // namespace
+
+// The attribute belongs to the device, and one process may drive several GPUs.
+void smem_attr(const void* fn, int bytes) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void*>> done;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.insert({dev, fn}).second) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
 
 int set_error(emul_handle_t h, int code, const std::string& msg) {
   if (h) h->last_error = msg;

@@ -56,6 +56,8 @@ struct Operand {
 };
 
 int set_error(emul_handle_t h, int code, const std::string& msg);
+// Raise a kernel's dynamic shared-memory limit to `bytes`, once per device.
+void smem_attr(const void* fn, int bytes);
 int check_cuda(emul_handle_t h, cudaError_t e, const char* what);
 
 // Grow the workspace to at least `bytes` (synchronises the device when it grows).

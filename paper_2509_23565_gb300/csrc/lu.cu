@@ -798,17 +798,6 @@ __global__ void probe_check_kernel(int m, int n, int k, const double* L, long ld
 }
 
 // ------------------------------------------------------------------ host helpers
-// Raise a kernel's dynamic shared-memory limit once per device: the attribute
-// belongs to the device, and one process may drive several GPUs.
-void smem_attr(const void* fn, int bytes) {
-  static std::mutex mu;
-  static std::set<std::pair<int, const void*>> done;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  std::lock_guard<std::mutex> lock(mu);
-  if (done.insert({dev, fn}).second) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
-
 struct LuBufs {
   double* inv;          // nb x nb
   uint64_t* recs;       // leaf pivot exchange: [2][nsm][kRecWords] epoch-tagged words

@@ -1,0 +1,230 @@
+// LU without pivoting whose every third-order step runs through the emulated
+// product: the Level-3-only factorization arXiv 2509.23565 times for blocking
+// factors 256 to 2048 (Section 6), with the Schur update of Eq. 7.
+//
+// Step j0 (right-looking, block nb):
+//   1. the panel A[j0:n, j0:j0+jb] is factored by recursive halving.  A leaf
+//      (<= 128 columns) factors its diagonal block in FP64 inside one CTA and
+//      forms the inverses of both triangular factors there; its rows below
+//      become L21 = A21 U11^-1 through the emulated product.  An inner node
+//      forms U12 = L11^-1 A12 and the Schur update of the rows below with the
+//      emulated product, recurses into its right half, and joins the two
+//      halves' unit-lower inverses, X21 = -X22 (L21 X11);
+//   2. U12 = X A12 with X = L11^-1 of the whole block (emulated product);
+//   3. A22 <- A22 - L21 U12 (emulated product, alpha = -1, beta = 1).
+// No row is ever exchanged, so the factorization is stable only for matrices
+// that need no pivoting (diagonally dominant, SPD).
+#include <cuda_runtime.h>
+
+#include "handle.h"
+
+namespace emul {
+namespace {
+
+constexpr int kNpLeaf = 128;          // widest diagonal block factored in one CTA
+constexpr int kNpThreads = 1024;      // 128 rows x 8 column groups
+constexpr int kNpPerThread = kNpLeaf / 8;
+constexpr size_t kNpAl = 256;
+
+inline size_t np_al(size_t x) { return (x + kNpAl - 1) / kNpAl * kNpAl; }
+
+// The w x w diagonal block at A[d.., d..] (w <= 128) is factored in place
+// without pivoting, A = L U (L unit lower), in shared memory; then
+// X <- L^-1 (ld ldx, zeros above the diagonal) and Y <- U^-1 (ld w, zeros
+// below).  A zero pivot leaves its column unscaled and records its 1-based
+// index in *info unless an earlier one is there.  Thread (r, g) = (tid % 128,
+// tid / 128) works on row r and the columns g, g + 8, ...; for the inverses
+// it holds those 16 entries of its row in registers, and the finished row k
+// is published through a double-buffered shared row.
+__global__ void __launch_bounds__(kNpThreads, 1) np_leaf_kernel(double* A, long lda, int d, int w, int32_t* info,
+                                                                double* X, long ldx, double* Y) {
+  extern __shared__ double S[];                  // w x w, leading dimension w + 1
+  __shared__ double rowbuf[2][kNpLeaf];
+  const int tid = threadIdx.x;
+  const int r = tid & (kNpLeaf - 1);
+  const int g = tid >> 7;
+  const int ld = w + 1;
+  double* D = A + d + static_cast<long>(d) * lda;
+  for (int j = g; j < w; j += 8)
+    if (r < w) S[r + j * ld] = D[r + static_cast<long>(j) * lda];
+  __syncthreads();
+  for (int k = 0; k < w; ++k) {
+    const double piv = S[k + k * ld];
+    if (g == 0 && r > k && r < w && piv != 0.0) S[r + k * ld] = S[r + k * ld] / piv;
+    if (tid == 0 && piv == 0.0) atomicCAS(info, 0, d + k + 1);
+    __syncthreads();
+    if (r > k && r < w) {
+      const double l = S[r + k * ld];
+      for (int j = k + 1 + g; j < w; j += 8) S[r + j * ld] = fma(-l, S[k + j * ld], S[r + j * ld]);
+    }
+    __syncthreads();
+  }
+  for (int j = g; j < w; j += 8)
+    if (r < w) D[r + static_cast<long>(j) * lda] = S[r + j * ld];
+
+  // X = L^-1: row r of X is e_r - sum_{k<r} L(r,k) X(k,:), accumulated k by k
+  double x[kNpPerThread];
+#pragma unroll
+  for (int t = 0; t < kNpPerThread; ++t) x[t] = (r == g + 8 * t) ? 1.0 : 0.0;
+  for (int k = 0; k + 1 < w; ++k) {
+    double* rb = rowbuf[k & 1];
+    if (r == k) {
+#pragma unroll
+      for (int t = 0; t < kNpPerThread; ++t) rb[g + 8 * t] = x[t];
+    }
+    __syncthreads();
+    if (r > k && r < w) {
+      const double l = S[r + k * ld];
+#pragma unroll
+      for (int t = 0; t < kNpPerThread; ++t) x[t] = fma(-l, rb[g + 8 * t], x[t]);
+    }
+  }
+  if (r < w) {
+#pragma unroll
+    for (int t = 0; t < kNpPerThread; ++t)
+      if (g + 8 * t < w) X[r + static_cast<long>(g + 8 * t) * ldx] = x[t];
+  }
+  __syncthreads();
+
+  // Y = U^-1: row r of Y is (e_r - sum_{k>r} U(r,k) Y(k,:)) / U(r,r), k from w-1 down
+#pragma unroll
+  for (int t = 0; t < kNpPerThread; ++t) x[t] = (r == g + 8 * t) ? 1.0 : 0.0;
+  for (int k = w - 1; k >= 0; --k) {
+    double* rb = rowbuf[k & 1];
+    if (r == k) {
+      const double u = S[k + k * ld];
+#pragma unroll
+      for (int t = 0; t < kNpPerThread; ++t) {
+        x[t] = x[t] / u;
+        rb[g + 8 * t] = x[t];
+      }
+    }
+    __syncthreads();
+    if (r < k) {
+      const double l = S[r + k * ld];
+#pragma unroll
+      for (int t = 0; t < kNpPerThread; ++t) x[t] = fma(-l, rb[g + 8 * t], x[t]);
+    }
+  }
+  if (r < w) {
+#pragma unroll
+    for (int t = 0; t < kNpPerThread; ++t)
+      if (g + 8 * t < w) Y[r + static_cast<long>(g + 8 * t) * w] = x[t];
+  }
+}
+
+struct NpBufs {
+  double* X;     // jb x jb, ld nb: L11^-1 of the current block
+  double* Y;     // 128 x 128: U^-1 of the current leaf
+  double* T;     // scratch for the inverse join, up to nb x nb
+  long ldx;
+};
+
+// Split of a w-column panel: the left part a multiple of 16 near w/2.
+inline int np_split(int w) {
+  const int w1 = (w / 2 + 15) / 16 * 16;
+  return w1 < w ? w1 : w / 2;
+}
+
+// Factor the panel A[d:n, d:d+w] (no pivoting) and leave L^-1 of its diagonal
+// block in X at (d - j0, d - j0).
+int np_panel(emul_handle_t h, double* A, long lda, int n, int j0, int d, int w, int s, int32_t* info,
+             const NpBufs& B) {
+  double* Xd = B.X + (d - j0) + static_cast<long>(d - j0) * B.ldx;
+  if (w <= kNpLeaf) {
+    const size_t smem = static_cast<size_t>(w) * (w + 1) * 8;
+    smem_attr(reinterpret_cast<const void*>(np_leaf_kernel), kNpLeaf * (kNpLeaf + 1) * 8);
+    np_leaf_kernel<<<1, kNpThreads, smem, h->stream>>>(A, lda, d, w, info, Xd, B.ldx, B.Y);
+    h->launches++;
+    int rc = check_cuda(h, cudaGetLastError(), "no-pivot leaf");
+    if (rc) return rc;
+    const int mb = n - d - w;
+    if (mb <= 0) return EMUL_OK;
+    double* A21 = A + (d + w) + static_cast<long>(d) * lda;
+    // L21 = A21 U11^-1, written over A21 (both operands are sliced before the product writes)
+    return gemm_run(h, mb, w, w, 1.0, Operand{A21, 1, lda}, Operand{B.Y, w, 1}, 0.0, A21, lda, s, false, 0,
+                    nullptr, 0, 0);
+  }
+  const int w1 = np_split(w), w2 = w - w1;
+  int rc = np_panel(h, A, lda, n, j0, d, w1, s, info, B);
+  if (rc) return rc;
+  double* A12 = A + d + static_cast<long>(d + w1) * lda;
+  // U12 = L11^-1 A12 (w1 x w2), over A12
+  rc = gemm_run(h, w1, w2, w1, 1.0, Operand{Xd, 1, B.ldx}, Operand{A12, lda, 1}, 0.0, A12, lda, s, false, 0, nullptr,
+                0, 0);
+  if (rc) return rc;
+  // Schur update of the right half, every row below the left half's diagonal block
+  const double* L21 = A + (d + w1) + static_cast<long>(d) * lda;
+  double* A22 = A + (d + w1) + static_cast<long>(d + w1) * lda;
+  rc = gemm_run(h, n - d - w1, w2, w1, -1.0, Operand{L21, 1, lda}, Operand{A12, lda, 1}, 1.0, A22, lda, s, false, 0,
+                nullptr, 0, 0);
+  if (rc) return rc;
+  rc = np_panel(h, A, lda, n, j0, d + w1, w2, s, info, B);
+  if (rc) return rc;
+  // join the inverses: X21 = -X22 (L21 X11), L21 the w2 x w1 block below the left diagonal block
+  double* X22 = Xd + w1 + static_cast<long>(w1) * B.ldx;
+  double* X21 = Xd + w1;
+  rc = gemm_run(h, w2, w1, w1, 1.0, Operand{L21, 1, lda}, Operand{Xd, B.ldx, 1}, 0.0, B.T, w2, s, false, 0, nullptr,
+                0, 0);
+  if (rc) return rc;
+  return gemm_run(h, w2, w1, w2, -1.0, Operand{X22, 1, B.ldx}, Operand{B.T, w2, 1}, 0.0, X21, B.ldx, s, false, 0,
+                  nullptr, 0, 0);
+}
+
+}  // namespace
+}  // namespace emul
+
+extern "C" {
+
+int emul_dgetrf_nopiv(emul_handle_t h, int n, double* A, int lda, int nb, int slices, int32_t* info,
+                      emul_stats* stats) {
+  using namespace emul;
+  if (!h) return EMUL_INVALID_ARG;
+  if (nb == 0) nb = 1024;
+  if (n < 0 || lda < (n > 1 ? n : 1) || nb < 16 || nb > 4096 || slices < 1 || slices > kMaxSlices ||
+      (n > 0 && (!A || !info)))
+    return set_error(h, EMUL_INVALID_ARG, "emul_dgetrf_nopiv: invalid argument");
+  if (stats) *stats = emul_stats{0, slices, slices, 0, 0.0, static_cast<double>(slices)};
+  if (n == 0) return EMUL_OK;
+  int rc = check_cuda(h, cudaMemsetAsync(info, 0, sizeof(int32_t), h->stream), "info reset");
+  if (rc) return rc;
+  const int nbe = nb < n ? nb : n;
+  // [product workspace | X (nbe x nbe) | Y (128 x 128) | T (nbe x nbe)]
+  const size_t gw = np_al(gemm_workspace_bytes(n, n, nbe, slices, false));
+  const size_t xb = np_al(8ull * nbe * nbe), yb = np_al(8ull * kNpLeaf * kNpLeaf);
+  rc = reserve_workspace(h, gw + 2 * xb + yb);
+  if (rc) return rc;
+  uint8_t* base = static_cast<uint8_t*>(h->ws);
+  const NpBufs B{reinterpret_cast<double*>(base + gw), reinterpret_cast<double*>(base + gw + xb),
+                 reinterpret_cast<double*>(base + gw + xb + yb), nbe};
+  for (int j0 = 0; j0 < n; j0 += nb) {
+    const int jb = nb < n - j0 ? nb : n - j0;
+    int ph = phase_begin(h, EMUL_PHASE_PANEL);
+    // the blocks of X above the diagonal are never written: zero them
+    rc = check_cuda(h, cudaMemsetAsync(B.X, 0, 8ull * nbe * jb, h->stream), "inverse reset");
+    if (rc) return rc;
+    rc = np_panel(h, A, lda, n, j0, j0, jb, slices, info, B);
+    phase_end(h, ph);
+    if (rc) return rc;
+    const int m2 = n - j0 - jb;
+    if (m2 > 0) {
+      ph = phase_begin(h, EMUL_PHASE_U12);
+      double* A12 = A + j0 + static_cast<long>(j0 + jb) * lda;
+      rc = gemm_run(h, jb, m2, jb, 1.0, Operand{B.X, 1, B.ldx}, Operand{A12, lda, 1}, 0.0, A12, lda, slices, false,
+                    0, nullptr, 0, 0);
+      phase_end(h, ph);
+      if (rc) return rc;
+      ph = phase_begin(h, EMUL_PHASE_UPDATE);
+      const double* L21 = A + (j0 + jb) + static_cast<long>(j0) * lda;
+      double* A22 = A + (j0 + jb) + static_cast<long>(j0 + jb) * lda;
+      rc = gemm_run(h, m2, m2, jb, -1.0, Operand{L21, 1, lda}, Operand{A12, lda, 1}, 1.0, A22, lda, slices, false, 0,
+                    nullptr, 0, 0);
+      phase_end(h, ph);
+      if (rc) return rc;
+    }
+    if (stats) stats->steps++;
+  }
+  return EMUL_OK;
+}
+
+}  // extern "C"

@@ -17,6 +17,14 @@ column-major (Fortran) order, the layout of the C-ABI.
 * parawilk_random(n, d, b, alpha, seed)
                                    Eq. 15: 2 u**2 (u ~ U(0, 1)) in the zero
                                    positions of parawilk, parawilk elsewhere.
+* diag_dominant(n, seed)           U(-1, 1) entries with n on the diagonal: strictly
+                                   diagonally dominant by rows and columns, so
+                                   elimination needs no pivoting (the no-pivot LU).
+* bidiag_factors(n, seed, zero_at) unit lower bidiagonal L and upper bidiagonal U
+                                   with integer entries (subdiagonal / superdiagonal
+                                   in {-1, 0, 1}, diagonal of U +-1, or 0 at zero_at)
+                                   and A = L U: every Schur complement and block
+                                   inverse of A is a small integer matrix.
 """
 import numpy as np
 
@@ -116,3 +124,21 @@ def mixed_range(n, nb, ranges, seed):
             rows = slice(i0, min(n, i0 + nb))
             A[rows, :] *= np.power(10.0, (rng.random((A[rows, :].shape)) * 2.0 - 1.0) * r)
     return np.asfortranarray(A)
+
+
+def diag_dominant(n, seed):
+    A = uniform(n, n, seed)
+    A[np.arange(n), np.arange(n)] = float(n)
+    return A
+
+
+def bidiag_factors(n, seed, zero_at=None):
+    rng = _rng(seed)
+    L = np.eye(n)
+    U = np.diag(rng.choice([-1.0, 1.0], size=n))
+    if n > 1:
+        L[np.arange(1, n), np.arange(n - 1)] = rng.integers(-1, 2, size=n - 1).astype(np.float64)
+        U[np.arange(n - 1), np.arange(1, n)] = rng.integers(-1, 2, size=n - 1).astype(np.float64)
+    if zero_at is not None:
+        U[zero_at, zero_at] = 0.0
+    return np.asfortranarray(L), np.asfortranarray(U), np.asfortranarray(L @ U)

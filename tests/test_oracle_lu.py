@@ -156,3 +156,43 @@ def test_table1_trend_parawilk256():
     # different draw and library)
     for got, want in zip(res, paper):
         assert want / 4 < got < want * 4, (res, paper)
+
+
+@pytest.mark.parametrize("n,nb", [(150, 32), (97, 16), (64, 64)])
+def test_getrf_nopiv_matches_lapack_without_interchanges(n, nb):
+    """Strictly column diagonally dominant A: partial pivoting keeps every
+    diagonal pivot (LAPACK's pivots are the identity), so the no-pivot LU
+    equals LAPACK's factors up to the summation order of the blocking."""
+    A = inputs.diag_dominant(n, seed=300 + n)
+    lu_ref, piv_ref = scipy.linalg.lu_factor(A)
+    assert (piv_ref == np.arange(n)).all()
+    LU, info = lu.getrf_nopiv(A, nb=nb)
+    assert info == 0
+    assert np.max(np.abs(LU - lu_ref)) <= 1e-13 * np.max(np.abs(lu_ref))
+
+
+@pytest.mark.parametrize("update", ["fp64", "emulated"])
+def test_getrf_nopiv_bidiagonal_exact(update):
+    """A = L U with integer bidiagonal factors: every quantity of the
+    elimination is a small integer, so both updates return L and U exactly."""
+    n = 100
+    L, U, A = inputs.bidiag_factors(n, seed=311)
+    LU, info = lu.getrf_nopiv(A, nb=16, update=update, s=7)
+    assert info == 0
+    assert np.array_equal(LU, np.tril(L, -1) + U)
+
+
+def test_getrf_nopiv_zero_pivot_info():
+    _, _, A = inputs.bidiag_factors(90, seed=312, zero_at=37)
+    _, info = lu.getrf_nopiv(A, nb=16)
+    assert info == 38
+
+
+@pytest.mark.parametrize("s,ok", [(8, True), (3, False)])
+def test_getrf_nopiv_emulated_residual(s, ok):
+    n = 128
+    A = inputs.diag_dominant(n, seed=320)
+    b = inputs.vector(n, seed=321)
+    LU, info = lu.getrf_nopiv(A, nb=32, update="emulated", s=s)
+    x = lu.getrs(LU, np.arange(1, n + 1), b)
+    assert (residual.scaled_residual(A, x, b) < 16) == ok
