@@ -459,7 +459,12 @@ int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Oper
     rc = check_cuda(h, cudaGetLastError(), "zero levels");
     if (rc) return rc;
   }
-  const bool wide = !narrow_ok(s, k, t);
+  // the narrow test plans a schedule; it is made once per (s, t, K chunks)
+  const uint64_t nkey = (static_cast<uint64_t>(s) << 32) | (static_cast<uint64_t>(t) << 16) |
+                        static_cast<uint64_t>((k + kBK - 1) / kBK);
+  auto nit = h->narrow_cache.find(nkey);
+  if (nit == h->narrow_cache.end()) nit = h->narrow_cache.emplace(nkey, narrow_ok(s, k, t)).first;
+  const bool wide = !nit->second;
   if (wide && mode == 0 && !wide_ok(s, t, k))
     return set_error(h, EMUL_NOT_SUPPORTED, "threshold too high for this k: the 128-bit Horner state could overflow");
   const int nch = (k + kBK - 1) / kBK;
