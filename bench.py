@@ -7,7 +7,7 @@ updates with s INT8 slices) plus the solve (emul_dgetrs).  The TFLOP/s
 numerator is the HPL count 2/3 n^3 + 3/2 n^2.  The backward error
 ||Ax-b|| / (||A|| ||x|| n eps) of the last solve must stay <= 16.
 
---workload lu_nopiv times the Level-3-only LU without pivoting of Section 6
+--workload lu_nopiv times the Level-3-only LU without pivoting of Section 8
 (emul_dgetrf_nopiv, block size --nb up to 4096) on a diagonally dominant
 matrix, with the same solve, checks and JSON keys.
 

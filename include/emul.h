@@ -149,7 +149,7 @@ int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int n
 
 /* LU without pivoting of the n x n matrix A (lda), in place, A = L U (L unit
  * lower, U upper): the Level-3-only factorization timed for blocking factors
- * 256 to 2048 (Section 6), right-looking with block size nb (16..4096; 0 =
+ * 256 to 2048 (Section 8), right-looking with block size nb (16..4096; 0 =
  * 1024).  Every third-order step runs through the emulated product with
  * `slices` slices: the Schur update A22 <- A22 - L21 U12 (Eq. 7), and the
  * triangular solves through explicit inverses of the diagonal blocks (a

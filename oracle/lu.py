@@ -96,7 +96,7 @@ def getf2_nopiv(P, info_state, offset):
 
 def getrf_nopiv(A, nb=64, update="fp64", s=7):
     """Right-looking blocked LU without pivoting, the Level-3-only variant of
-    Section 6: panel by unblocked elimination, U12 = L11^{-1} A12, then the
+    Section 8: panel by unblocked elimination, U12 = L11^{-1} A12, then the
     Schur complement of Eq. 7.  Returns (LU, info)."""
     A = np.array(A, dtype=np.float64, order="F", copy=True)
     n = A.shape[0]

@@ -1,6 +1,6 @@
 // LU without pivoting whose every third-order step runs through the emulated
 // product: the Level-3-only factorization arXiv 2509.23565 times for blocking
-// factors 256 to 2048 (Section 6), with the Schur update of Eq. 7.
+// factors 256 to 2048 (Section 8), with the Schur update of Eq. 7.
 //
 // Step j0 (right-looking, block nb):
 //   1. the panel A[j0:n, j0:j0+jb] is factored by recursive halving.  A leaf

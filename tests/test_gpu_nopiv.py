@@ -1,4 +1,4 @@
-"""GPU LU without pivoting (the Level-3-only factorization of Section 6)
+"""GPU LU without pivoting (the Level-3-only factorization of Section 8)
 through the C-ABI, checked against the oracle.
 
 * Integer bidiagonal factors: every Schur complement and block inverse is a
