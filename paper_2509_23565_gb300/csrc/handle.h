@@ -24,7 +24,7 @@ struct emul_handle_s {
     int nsweeps;
     emul::SlotPlan plan;
   };
-  std::map<uint32_t, SchedEntry> sched_cache;   // (s, wide, level-sum mode, chunks) -> device schedule
+  std::map<uint32_t, SchedEntry> sched_cache;   // (s, wide, level-sum mode, threshold, chunks) -> device schedule
   std::map<uint64_t, bool> narrow_cache;        // (s, t, chunks) -> the 128-column variant applies
   std::string last_error;
   void* encode_fn = nullptr;        // cuTensorMapEncodeTiled
