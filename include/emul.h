@@ -153,7 +153,7 @@ int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int n
  * 1024).  Every third-order step runs through the emulated product with
  * `slices` slices: the Schur update A22 <- A22 - L21 U12 (Eq. 7), and the
  * triangular solves through explicit inverses of the diagonal blocks (a
- * panel is halved recursively down to blocks of at most 128 columns, factored
+ * panel is halved recursively down to blocks of at most 64 columns, factored
  * in FP64).  No rows are exchanged, so the result is only as stable as
  * Gaussian elimination without pivoting on A (diagonally dominant or SPD
  * matrices need none).  A zero pivot sets *info to its 1-based index (the
@@ -261,10 +261,11 @@ int emul_selector_load(emul_handle_t h, const char* path);
 
 /* -------------------------------------------------------- no allocation --
  * emul_dgemm without any device allocation, for callers that cannot call
- * cudaMalloc: code that runs while a stream is being captured into a CUDA
- * graph, or a host library whose device memory is owned by another allocator
- * (a framework's caching allocator, a memory pool sized at start-up).  The
- * paper has no counterpart to this entry point.
+ * cudaMalloc: a host library whose device memory is owned by another
+ * allocator (a framework's caching allocator, a memory pool sized at
+ * start-up), or a latency-bound loop that must not call cudaMalloc or
+ * cudaFree because either can synchronise the whole device.  The paper has no
+ * counterpart to this entry point.
  *
  * Same arguments and results as emul_dgemm, but on `stream` (a cudaStream_t)
  * instead of a handle.  The scratch (slices, scales, schedule, status word)
@@ -291,7 +292,8 @@ typedef struct emul_profile {
   long long kernel_launches;    /* kernels launched by this handle since the last read */
   long long product_launches;   /* launches of the slice-pair product kernel */
   double product_ms;            /* their summed device time (CUDA events) */
-  double product_tensor_flops;  /* sum of 2 m n k P (P = s(s+1)/2 slice-pair products) */
+  double product_tensor_flops;  /* sum of 2 m n k P, P the slice pairs kept: sum over the levels
+                                   L = 2..t of their pairs (s(s+1)/2 at the default t = s + 1) */
   double product_bytes;         /* algorithmic bytes: C read + write (8 B each) and the slices read */
   double phase_ms[5];           /* device time of the factorization phases (CUDA events around each),
                                    indexed by EMUL_PHASE_* */

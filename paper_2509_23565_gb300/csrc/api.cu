@@ -526,7 +526,9 @@ int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Oper
       }
       (i == 0 ? rec.e0 : rec.e1) = ev;
     }
-    const double P = static_cast<double>(s) * (s + 1) / 2.0;
+    // slice pairs kept: those of the levels L = 2..t (s(s+1)/2 at t = s + 1)
+    double P = 0.0;
+    for (int L = 2; L <= t; ++L) P += pairs_at(s, L);
     const double cells = lower ? 0.5 * m * (double)n : static_cast<double>(m) * n;
     rec.flops = 2.0 * cells * k * P;
     rec.bytes = cells * (beta != 0.0 ? 16.0 : 8.0) + static_cast<double>(s) * 2.0 * k * (m + (same ? 0 : n));
@@ -756,10 +758,12 @@ int emul_dgemm(emul_handle_t h, int m, int n, int k, double alpha, const double*
 
 // ---------------------------------------------------------------------------
 // emul_dgemm_noalloc: the emulated DGEMM for callers that cannot allocate
-// device memory (for example code running inside a stream capture that must
-// not allocate, or a host library whose allocator is owned by someone else).
-// All scratch lives in one file-scope device array of kNoAllocScratchBytes
-// that every GPU which loads this library keeps until the process exits.
+// device memory: a host library whose device memory belongs to another
+// allocator (a framework's caching allocator, a pool sized at start-up), or a
+// latency-bound loop that must not call cudaMalloc / cudaFree (both can
+// synchronise the whole device).  All scratch lives in one file-scope device
+// array of kNoAllocScratchBytes that every GPU which loads this library keeps
+// until the process exits.
 namespace emul {
 namespace {
 

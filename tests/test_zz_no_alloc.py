@@ -52,6 +52,23 @@ def test_noalloc_matches_dgemm_twice(gpu_lib):
         assert np.array_equal(r.view(np.int64), g.view(np.int64))
 
 
+def test_noalloc_matches_oracle(gpu_lib):
+    """One call checked straight against the oracle's emulated product: the
+    exact level sums rounded once, then C = RN(RN(alpha D) + RN(beta C))."""
+    import torch
+    from oracle import emulgemm
+    fn = _noalloc()
+    m, n, k, s, alpha, beta = 200, 170, 300, 7, -1.0, 1.0
+    A = inputs.log_scaled(m, k, 4, seed=31)
+    B = inputs.uniform(k, n, seed=32)
+    C = inputs.uniform(m, n, seed=33)
+    got = ColMajor.from_numpy(C)
+    assert _call(fn, ColMajor.from_numpy(A), ColMajor.from_numpy(B), got, s, alpha, beta) == 0
+    torch.cuda.synchronize()
+    want = emulgemm.emul_gemm(A, B, s, alpha=alpha, beta=beta, C=C)
+    assert np.array_equal(got.numpy().view(np.int64), want.view(np.int64))
+
+
 def test_noalloc_rejects_oversize(gpu_lib):
     fn = _noalloc()
     m = n = 4096
