@@ -9,7 +9,10 @@ numerator is the HPL count 2/3 n^3 + 3/2 n^2.  The backward error
 
 --workload lu_nopiv times the Level-3-only LU without pivoting of Section 8
 (emul_dgetrf_nopiv, block size --nb up to 4096) on a diagonally dominant
-matrix, with the same solve, checks and JSON keys.
+matrix, with the same solve, checks and JSON keys.  --range R > 0 draws the LU
+input from the log-scaled generator u 10^e, e ~ U(-R, R).  --workload chol
+times the blocked Cholesky (emul_dpotrf + emul_dpotrs) of an SPD matrix
+Q diag(lam) Q^T with condition number --cond (numerator n^3/3 + 2 n^2).
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle (the
 project's plain reference of the same method) on a bounded sample.
@@ -30,6 +33,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "emulated-FP64 LU TFLOP/s vs native-FP64 LU on one GB300 at backward error ≤16"
 METRIC_NOPIV = "emulated-FP64 LU without pivoting TFLOP/s on one GB300 at backward error ≤16"
+METRIC_CHOL = "emulated-FP64 Cholesky TFLOP/s vs native-FP64 Cholesky on one GB300 at backward error ≤16"
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum (673.4 + 516.2 MB) over the algorithmic
@@ -39,6 +43,10 @@ TRAFFIC_RATIO = (673.37e6 + 516.18e6) / (8192.0 * 8192.0 * 16.0 + 2 * 7 * 8192 *
 
 def lu_flops(n):
     return 2.0 / 3.0 * n ** 3 + 1.5 * n ** 2
+
+
+def chol_flops(n):
+    return n ** 3 / 3.0 + 2.0 * n ** 2
 
 
 def measured_peaks():
@@ -128,32 +136,74 @@ def max_over_ranks(world, x):
     return float(t.item())
 
 
-def aggregate_value(world, n, steps, ms_max):
-    """Whole-job TFLOP/s of `world` replicas, each factoring one n x n matrix per step."""
-    return world * lu_flops(n) * steps / (ms_max / 1e3) / 1e12
+def aggregate_value(world, flops_per_step, steps, ms_max):
+    """Whole-job TFLOP/s of `world` replicas, each doing flops_per_step per step."""
+    return world * flops_per_step * steps / (ms_max / 1e3) / 1e12
 
 
-def cpu_oracle_lu(n, nb, s, seed, nopiv=False):
-    """Time the oracle's emulated LU + solve of one n x n matrix (bounded sample)."""
+def cpu_oracle_lu(n, nb, s, seed, nopiv=False, update="emulated"):
+    """Time the oracle's LU + solve of one n x n matrix (bounded sample):
+    update = "emulated" (the method, s slices) or "fp64" (FP64 trailing updates)."""
     from oracle import lu as olu, residual
     from paper_2509_23565_gb300 import inputs
     A = inputs.diag_dominant(n, seed=seed) if nopiv else inputs.uniform(n, n, seed=seed)
     b = inputs.vector(n, seed=seed + 1)
     t0 = time.perf_counter()
     if nopiv:
-        LU, _ = olu.getrf_nopiv(A, nb=nb, update="emulated", s=s)
+        LU, _ = olu.getrf_nopiv(A, nb=nb, update=update, s=s)
         piv = np.arange(1, n + 1)
     else:
-        LU, piv, _ = olu.getrf(A, nb=nb, update="emulated", s=s)
+        LU, piv, _ = olu.getrf(A, nb=nb, update=update, s=s)
     x = olu.getrs(LU, piv, b)
     dt = time.perf_counter() - t0
     return dt, residual.backward_error(A, x, b)
 
 
+def cpu_oracle_chol(n, nb, cond, seed):
+    """Time the oracle's FP64 blocked Cholesky + solve of one SPD n x n matrix."""
+    from oracle import lu as olu, residual
+    from paper_2509_23565_gb300 import inputs
+    A = inputs.spd(n, cond, seed=seed)
+    b = inputs.vector(n, seed=seed + 1)
+    t0 = time.perf_counter()
+    L, _ = olu.potrf(A, nb=nb, update="fp64")
+    x = olu.potrs(L, b)
+    dt = time.perf_counter() - t0
+    return dt, residual.backward_error(A, x, b)
+
+
+def cpu_baseline(args, kind, s):
+    """The oracle as it stands on the host cores, on bounded samples of the
+    workload: its FP64 blocked factorization + solve (numpy BLAS threads for the
+    trailing updates, the panel loop single-threaded) and, for LU, its emulated
+    LU + solve with s slices (exact recombination in Python integers)."""
+    cores = os.cpu_count()
+    if kind == "chol":
+        n = 2 * args.cpu_n
+        dt, be = cpu_oracle_chol(n, 256, args.cond, 1234)
+        return {"value": chol_flops(n) / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+                "sample": f"oracle FP64 blocked Cholesky + solve of one SPD n={n} matrix (cond {args.cond:g}, "
+                          f"nb=256; numpy BLAS threads, panel loop single-threaded)",
+                "seconds": dt, "backward_error": be}
+    nopiv = kind == "lu_nopiv"
+    n = args.cpu_n
+    dt, be = cpu_oracle_lu(n, 256, s, 1234, nopiv, update="fp64")
+    edt, ebe = cpu_oracle_lu(args.cpu_emul_n, 64, s, 1235, nopiv, update="emulated")
+    what = "no-pivot LU" if nopiv else "LU with partial pivoting"
+    return {"value": lu_flops(n) / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+            "sample": f"oracle FP64 blocked {what} + solve of one n={n} uniform(-1,1) matrix (nb=256; numpy BLAS "
+                      f"threads for the trailing updates, panel loop single-threaded)",
+            "seconds": dt, "backward_error": be,
+            "emulated_sample": {"value": lu_flops(args.cpu_emul_n) / edt / 1e12, "unit": "TFLOP/s",
+                                "sample": f"oracle emulated {what} + solve of one n={args.cpu_emul_n} matrix "
+                                          f"(nb=64, s={s}; exact recombination single-threaded)",
+                                "seconds": edt, "backward_error": ebe}}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    n = args.cpu_n
+    n = args.cpu_emul_n
     for _ in range(args.warmup):
         cpu_oracle_lu(n, 64, args.slices, 1000)
     times, berr = [], None
@@ -185,26 +235,42 @@ def run_ours(args, world, rank, local):
 
     torch.cuda.set_device(local)
     n, nb, s = args.n, args.nb, args.slices
-    nopiv = args.workload == "lu_nopiv"
+    kind = args.workload                  # lu, lu_nopiv, chol
+    nopiv = kind == "lu_nopiv"
+    chol = kind == "chol"
+    flops = chol_flops if chol else lu_flops
     seed = 7000 + rank
-    # Fortran order; the no-pivot LU needs a matrix that elimination without pivoting keeps stable
-    A_host = inputs.diag_dominant(n, seed=seed) if nopiv else inputs.uniform(n, n, seed=seed)
+    A_host = None
+    if chol:
+        A0 = inputs.spd_device(n, args.cond, seed=seed)              # symmetric: store = matrix
+    elif args.range > 0:
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(seed)
+        A0 = inputs.log_scaled_device(n, n, args.range, gen)         # store (n, n): column-major A
+    else:
+        # Fortran order; the no-pivot LU needs a matrix that elimination without pivoting keeps stable
+        A_host = inputs.diag_dominant(n, seed=seed) if nopiv else inputs.uniform(n, n, seed=seed)
+        A0 = torch.from_numpy(np.ascontiguousarray(A_host.T)).cuda()
     b_host = inputs.vector(n, seed=seed + 1)
-    A0 = torch.from_numpy(np.ascontiguousarray(A_host.T)).cuda()   # store (n, n): column-major A
     b0 = torch.from_numpy(b_host).cuda()
     work = ColMajor(torch.empty_like(A0), n, n)
     xb = ColMajor(torch.empty((1, n), dtype=torch.float64, device="cuda"), n, 1)
     lib = Emul()
     stream = torch.cuda.current_stream()
 
-    factor = lib.dgetrf_nopiv if nopiv else lib.dgetrf
+    def factor_solve():
+        if chol:
+            info = lib.dpotrf(work, nb=nb, slices=s)
+            lib.dpotrs(work, xb)
+            return info
+        ipiv, info = (lib.dgetrf_nopiv if nopiv else lib.dgetrf)(work, nb=nb, slices=s)
+        lib.dgetrs(work, ipiv, xb)
+        return info
 
     def step():
         work.store.copy_(A0)
         xb.store[0].copy_(b0)
-        ipiv, info = factor(work, nb=nb, slices=s)
-        lib.dgetrs(work, ipiv, xb)
-        return ipiv, info
+        return factor_solve()
 
     for _ in range(args.warmup):
         step()
@@ -224,7 +290,7 @@ def run_ours(args, world, rank, local):
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        ipiv, info = step()
+        info = step()
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -240,7 +306,7 @@ def run_ours(args, world, rank, local):
     berr = lib.backward_error(A_chk, xb, b_chk).cpu().numpy()
     info_v = int(info.item())
 
-    value = aggregate_value(world, n, args.steps, ms_max)
+    value = aggregate_value(world, flops(n), args.steps, ms_max)
     peaks, peak_kind = measured_peaks()
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
     achieved = prof["product_tensor_flops"] / (prof["product_ms"] / 1e3) / 1e12 if prof["product_ms"] > 0 else 0.0
@@ -258,15 +324,25 @@ def run_ours(args, world, rank, local):
                 "avg_launch_ms": prof["product_ms"] / max(1, prof["product_launches"]),
                 "share_of_step": prof["product_ms"] / ms}
 
-    workload = (f"LU without pivoting + solve, n={n} nb={nb} s={s}, A iid uniform(-1,1) with n on the diagonal, "
-                f"b uniform(-1,1)" if nopiv else
-                f"LU partial pivoting + solve, n={n} nb={nb} s={s}, A and b iid uniform(-1,1)")
+    if chol:
+        workload = (f"Cholesky + solve, n={n} nb={nb} s={s}, SPD A = Q diag(lam) Q^T (Q from the QR of a Gaussian "
+                    f"matrix, lam log-spaced 1..1/{args.cond:g}), b uniform(-1,1)")
+    elif nopiv:
+        workload = (f"LU without pivoting + solve, n={n} nb={nb} s={s}, A iid uniform(-1,1) with n on the diagonal, "
+                    f"b uniform(-1,1)")
+    elif args.range > 0:
+        workload = (f"LU partial pivoting + solve, n={n} nb={nb} s={s}, A = u 10^e with u uniform(-1,1), "
+                    f"e uniform(-{args.range:g},{args.range:g}); b uniform(-1,1)")
+    else:
+        workload = f"LU partial pivoting + solve, n={n} nb={nb} s={s}, A and b iid uniform(-1,1)"
+    metric = METRIC_CHOL if chol else METRIC_NOPIV if nopiv else METRIC
     result = {
-        "metric": METRIC_NOPIV if nopiv else METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "metric": metric, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload,
                    "n": n, "nb": nb, "slices": s, "parallelism": "replicas" if world > 1 else "single",
+                   **({"cond": args.cond} if chol else {"range": args.range} if args.range > 0 else {}),
                    "l2": "inputs (8 n^2 bytes) larger than L2; each step restores A from a device copy"},
         "backward_error": float(berr[1]), "scaled_residual_eq8": float(berr[0]), "info": info_v,
         "roofline": roofline, "gpu_launches": int(prof["kernel_launches"]), "clocks": clk,
@@ -275,7 +351,10 @@ def run_ours(args, world, rank, local):
 
     if rank == 0 and not args.no_e2e:
         # end to end through the C-ABI with host buffers: H2D of A and b, factor, solve, D2H of x
-        A_pin = torch.from_numpy(np.ascontiguousarray(A_host.T)).pin_memory()
+        if A_host is not None:
+            A_pin = torch.from_numpy(np.ascontiguousarray(A_host.T)).pin_memory()
+        else:
+            A_pin = A0.cpu().pin_memory()
         b_pin = torch.from_numpy(b_host).pin_memory()
         x_pin = torch.empty(n, dtype=torch.float64).pin_memory()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -285,45 +364,50 @@ def run_ours(args, world, rank, local):
         for _ in range(args.e2e_steps):
             work.store.copy_(A_pin, non_blocking=True)
             xb.store[0].copy_(b_pin, non_blocking=True)
-            ipiv, info = factor(work, nb=nb, slices=s)
-            lib.dgetrs(work, ipiv, xb)
+            factor_solve()
             x_pin.copy_(xb.store[0], non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
         e_ms = e0.elapsed_time(e1)
-        result["e2e"] = {"value": lu_flops(n) * args.e2e_steps / (e_ms / 1e3) / 1e12, "unit": "TFLOP/s",
+        result["e2e"] = {"value": flops(n) * args.e2e_steps / (e_ms / 1e3) / 1e12, "unit": "TFLOP/s",
                          "h2d_bytes_per_step": 8 * n * n + 8 * n, "d2h_bytes_per_step": 8 * n,
                          "steps": args.e2e_steps}
         del A_pin
 
     if rank == 0 and not args.no_native:
-        # native FP64 LU (cuSOLVER through torch) on the same GPU and input, with its backward error
+        # native FP64 factorization + solve (cuSOLVER through torch) on the same GPU and
+        # input, with its backward error; one untimed full-size call first (handles,
+        # workspace), then the timed one
         Am = A0.t()                        # column-major view of A
+
+        def native():
+            if chol:
+                Lc = torch.linalg.cholesky(Am)
+                return torch.cholesky_solve(b0.view(n, 1), Lc)
+            LU, piv = torch.linalg.lu_factor(Am, pivot=not nopiv)
+            return torch.linalg.lu_solve(LU, piv, b0.view(n, 1))
+
+        native()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        LU, piv = torch.linalg.lu_factor(Am, pivot=not nopiv)
-        x = torch.linalg.lu_solve(LU, piv, b0.view(n, 1))
+        x = native()
         e1.record(stream)
         torch.cuda.synchronize()
         nms = e0.elapsed_time(e1)
         xn = ColMajor(x.t().contiguous(), n, 1)
         nb_err = lib.backward_error(A_chk, xn, b_chk).cpu().numpy()
-        result["native_fp64"] = {"value": lu_flops(n) / (nms / 1e3) / 1e12, "unit": "TFLOP/s", "ms": nms,
-                                 "backward_error": float(nb_err[1]),
-                                 "impl": "torch.linalg.lu_factor/lu_solve" + (" (pivot=False)" if nopiv else "")}
+        impl = ("torch.linalg.cholesky/cholesky_solve" if chol else
+                "torch.linalg.lu_factor/lu_solve" + (" (pivot=False)" if nopiv else ""))
+        result["native_fp64"] = {"value": flops(n) / (nms / 1e3) / 1e12, "unit": "TFLOP/s", "ms": nms,
+                                 "backward_error": float(nb_err[1]), "impl": impl, "warmup": 1}
         result["speedup_vs_native"] = result["native_fp64"]["ms"] / result["ms_per_step"]
-        del LU, piv, x
+        del x
+        torch.cuda.empty_cache()
 
     if rank == 0 and not args.no_cpu:
-        dt, cberr = cpu_oracle_lu(args.cpu_n, 64, s, 1234, nopiv)
-        result["cpu_baseline"] = {"value": lu_flops(args.cpu_n) / dt / 1e12, "unit": "TFLOP/s",
-                                  "cores": os.cpu_count(), "kind": "oracle",
-                                  "sample": f"oracle emulated {'no-pivot ' if nopiv else ''}LU + solve of one "
-                                            f"n={args.cpu_n} matrix (nb=64, "
-                                            f"s={s}; numpy BLAS threads, exact recombination single-threaded)",
-                                  "seconds": dt}
+        result["cpu_baseline"] = cpu_baseline(args, kind, s)
     if rank == 0:
         print(json.dumps(result), flush=True)
 
@@ -501,13 +585,20 @@ def main():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="lu", choices=["lu", "lu_nopiv", "gemm", "selector", "batched", "table2"])
+    p.add_argument("--workload", default="lu",
+                   choices=["lu", "lu_nopiv", "chol", "gemm", "selector", "batched", "table2"])
+    p.add_argument("--range", type=float, default=0.0,
+                   help="LU input u 10^e, e ~ U(-range, range) (0: uniform(-1,1))")
+    p.add_argument("--cond", type=float, default=1e12, help="condition number of the Cholesky input")
     p.add_argument("--batch-count", type=int, default=4096)
     p.add_argument("--k", type=int, default=256)
     p.add_argument("--n", type=int, default=32768)
     p.add_argument("--nb", type=int, default=0, help="block size (0: 256 for lu, 1024 for lu_nopiv)")
     p.add_argument("--slices", type=int, default=7)
-    p.add_argument("--cpu-n", type=int, default=512)
+    p.add_argument("--cpu-n", type=int, default=3072,
+                   help="size of the oracle's FP64 factorization sample (Cholesky: twice this)")
+    p.add_argument("--cpu-emul-n", type=int, default=512,
+                   help="size of the oracle's emulated LU sample (and of each --impl reference step)")
     p.add_argument("--e2e-steps", type=int, default=1)
     p.add_argument("--no-native", action="store_true")
     p.add_argument("--no-e2e", action="store_true")

@@ -6,6 +6,9 @@
   ||b|| term, hence never smaller than Eq. 8).
 * lu_residual / chol_residual: factorization residuals ||PA - LU||_inf /
   (||A||_inf n eps) and ||A - LL^T||_inf / (||A||_inf n eps).
+* lu_residual_rows / chol_residual_rows: the same quotient with the infinity
+  norm of the numerator taken over the given rows only (a lower bound of the
+  full residual, for sizes where the full product L U is too costly here).
 
 Reading: eps = 2**-53, the unit roundoff of FP64 (LAPACK dlamch('E')), which the
 paper does not define.
@@ -72,3 +75,27 @@ def chol_residual(A, Lfac):
     n = A.shape[0]
     L = np.tril(np.asarray(Lfac, dtype=np.float64))
     return _inf_norm(A - L @ L.T) / (_inf_norm(A) * n * EPS)
+
+
+def lu_residual_rows(A, LU, ipiv, rows):
+    """max over the given rows i of sum_j |(PA - LU)_ij|, over ||A||_inf n eps."""
+    A = np.asarray(A, dtype=np.float64)
+    LU = np.asarray(LU, dtype=np.float64)
+    n = A.shape[0]
+    rows = np.asarray(rows)
+    perm = permutation_from_ipiv(ipiv, n)
+    cols = np.arange(n)[None, :]
+    Lr = np.where(cols < rows[:, None], LU[rows, :], 0.0)     # strictly lower part of row i of L
+    Lr[np.arange(len(rows)), rows] = 1.0                        # unit diagonal
+    R = A[perm[rows], :] - Lr @ np.triu(LU)
+    return float(np.max(np.sum(np.abs(R), axis=1))) / (_inf_norm(A) * n * EPS)
+
+
+def chol_residual_rows(A, Lfac, rows):
+    """max over the given rows i of sum_j |(A - LL^T)_ij|, over ||A||_inf n eps."""
+    A = np.asarray(A, dtype=np.float64)
+    L = np.tril(np.asarray(Lfac, dtype=np.float64))
+    n = A.shape[0]
+    rows = np.asarray(rows)
+    R = A[rows, :] - L[rows, :] @ L.T
+    return float(np.max(np.sum(np.abs(R), axis=1))) / (_inf_norm(A) * n * EPS)

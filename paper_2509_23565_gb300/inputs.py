@@ -17,6 +17,13 @@ column-major (Fortran) order, the layout of the C-ABI.
 * parawilk_random(n, d, b, alpha, seed)
                                    Eq. 15: 2 u**2 (u ~ U(0, 1)) in the zero
                                    positions of parawilk, parawilk elsewhere.
+* uniform_device, log_scaled_device
+                                   the same distributions drawn on the GPU with a seeded
+                                   torch.Generator (column-major device stores).
+* spd_device(n, cond, seed)        the spd() recipe drawn and formed on the GPU in FP64
+                                   (torch: seeded normal draws, QR, Q diag(lam) Q^T) for the
+                                   large sizes; returned as a device tensor (symmetric, so
+                                   row-major and column-major storage coincide).
 * diag_dominant(n, seed)           U(-1, 1) entries with n on the diagonal: strictly
                                    diagonally dominant by rows and columns, so
                                    elimination needs no pivoting (the no-pivot LU).
@@ -65,6 +72,22 @@ def spd(n, cond, seed):
     return np.asfortranarray(A)
 
 
+def spd_device(n, cond, seed, device="cuda"):
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    G = torch.randn((n, n), generator=gen, device=device, dtype=torch.float64)
+    Q, R = torch.linalg.qr(G)
+    del G
+    Q *= torch.sign(torch.diagonal(R))[None, :]
+    del R
+    lam = torch.logspace(0.0, -float(np.log10(cond)), n, device=device, dtype=torch.float64)
+    A = (Q * lam[None, :]) @ Q.T
+    del Q
+    A = 0.5 * (A + A.T)
+    return A.contiguous()
+
+
 def turing(n):
     A = np.eye(n) - np.tril(np.ones((n, n)), -1)
     return np.asfortranarray(A)
@@ -98,6 +121,19 @@ def batch_sizes(count, lo, hi, seed):
     """Log-uniform integer sizes in [lo, hi] for the batched solver."""
     rng = _rng(seed)
     return np.floor(np.exp(rng.uniform(np.log(lo), np.log(hi + 1), count))).astype(np.int64).clip(lo, hi)
+
+
+def uniform_device(m, n, seed, lo=-1.0, hi=1.0, device="cuda"):
+    """iid U(lo, hi) drawn on the device with a seeded torch.Generator;
+    returned as a column-major store (n x m tensor: row j is column j).  For
+    the large sizes, where drawing on the host takes minutes."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    x = torch.rand((n, m), generator=gen, device=device, dtype=torch.float64)
+    x *= (hi - lo)
+    x += lo
+    return x
 
 
 def log_scaled_device(m, n, r, gen, device="cuda"):

@@ -49,7 +49,7 @@ def _rank_main(rank, world, port, q):
     ms = [1000.0, 1500.0][rank]
     mx = bench.max_over_ranks(world, ms)
     bench.barrier(world)
-    q.put((rank, mx, bench.aggregate_value(world, 1024, 3, mx)))
+    q.put((rank, mx, bench.aggregate_value(world, bench.lu_flops(1024), 3, mx)))
     dist.destroy_process_group()
 
 

@@ -59,11 +59,12 @@ def test_getrf_getrs_uniform(gpu_lib, n, nb, s):
 
 
 @pytest.mark.parametrize("r", [4, 8, 16])
-def test_getrf_log_scaled(gpu_lib, r):
+@pytest.mark.parametrize("s", [7, 8])
+def test_getrf_log_scaled(gpu_lib, r, s):
     n = 512
     A = inputs.log_scaled(n, n, r, seed=30 + r)
     b = inputs.vector(n, seed=31)
-    dA, ipiv, info = _factor(gpu_lib, A, 64, 8)
+    dA, ipiv, info = _factor(gpu_lib, A, 64, s)
     assert info == 0
     db = ColMajor.from_numpy(b)
     gpu_lib.dgetrs(dA, ipiv, db)

@@ -196,3 +196,34 @@ def test_getrf_nopiv_emulated_residual(s, ok):
     LU, info = lu.getrf_nopiv(A, nb=32, update="emulated", s=s)
     x = lu.getrs(LU, np.arange(1, n + 1), b)
     assert (residual.scaled_residual(A, x, b) < 16) == ok
+
+
+def test_sampled_row_residuals_pinned():
+    """The sampled-row residuals equal the full ones when every row is taken
+    (up to the rounding of the products, which BLAS may sum in another order),
+    with the row order of P A from ipiv (a swap planted in the pivots shows),
+    and see an error planted in one row of L only through that row."""
+    n = 90
+    A = inputs.uniform(n, n, seed=181)
+    LU, ipiv, _ = lu.getrf(A, nb=16)
+    rows = np.arange(n)
+    assert abs(residual.lu_residual_rows(A, LU, ipiv, rows) - residual.lu_residual(A, LU, ipiv)) < 0.5
+    j = int(np.flatnonzero(ipiv != np.arange(1, n + 1))[0])
+    bad = ipiv.copy()
+    bad[j] = j + 1                                               # drop one interchange
+    assert residual.lu_residual_rows(A, LU, bad, rows) > 1e10
+    # an error in L(40, 0) changes row 40 of P A - L U and nothing else
+    LU2 = LU.copy()
+    LU2[40, 0] += 1e-6
+    others = rows[rows != 40]
+    assert residual.lu_residual_rows(A, LU2, ipiv, others) == residual.lu_residual_rows(A, LU, ipiv, others)
+    assert residual.lu_residual_rows(A, LU2, ipiv, [40]) > 1e6
+    S = inputs.spd(70, 1e4, seed=182)
+    L, info = lu.potrf(S, nb=16)
+    assert info == 0
+    assert abs(residual.chol_residual_rows(S, L, np.arange(70)) - residual.chol_residual(S, L)) < 0.5
+    L2 = L.copy()
+    L2[50, 3] += 1e-6     # row 50 of L L^T changes, and column 50 in the rows i >= 3 (L(i, 3) != 0)
+    assert residual.chol_residual_rows(S, L2, [50]) > 1e6
+    assert residual.chol_residual_rows(S, L2, [20]) > 1e3
+    assert residual.chol_residual_rows(S, L2, [0, 1, 2]) == residual.chol_residual_rows(S, L, [0, 1, 2])
