@@ -595,7 +595,7 @@ def main():
     p.add_argument("--n", type=int, default=32768)
     p.add_argument("--nb", type=int, default=0, help="block size (0: 256 for lu, 1024 for lu_nopiv)")
     p.add_argument("--slices", type=int, default=7)
-    p.add_argument("--cpu-n", type=int, default=3072,
+    p.add_argument("--cpu-n", type=int, default=4096,
                    help="size of the oracle's FP64 factorization sample (Cholesky: twice this)")
     p.add_argument("--cpu-emul-n", type=int, default=512,
                    help="size of the oracle's emulated LU sample (and of each --impl reference step)")

@@ -304,7 +304,10 @@ typedef struct emul_profile {
  * SWAP   the panel's row interchanges applied to the columns outside it,
  * U12    L11^-1 and U12 = L11^-1 A12,
  * UPDATE the trailing update A22 - L21 U12 (slicing, product, selector probe),
- * SOLVE  emul_dgetrs. */
+ * SOLVE  emul_dgetrs.
+ * emul_dpotrf / emul_dpotrs use the same slots: PANEL the diagonal block
+ * (L11 and L11^-1), U12 the product L21 = A21 L11^-T, UPDATE the lower
+ * trailing update A22 - L21 L21^T, SOLVE emul_dpotrs. */
 #define EMUL_PHASE_PANEL 0
 #define EMUL_PHASE_SWAP 1
 #define EMUL_PHASE_U12 2

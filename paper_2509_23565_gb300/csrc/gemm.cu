@@ -189,48 +189,52 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kLowRegs));
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
+    // the whole warp runs the loop (warp-uniform values); one elected lane issues
     if (lane == 0) {
       prefetch_tmap(&tmA);
       prefetch_tmap(&tmB);
-      long it = 0;
-      bool ok = true;
-      for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
-        int tm, tn;
-        tile_coords(a, tile, tm, tn);
-        const int m0 = tm * Cf::BM, n0 = tn * Cf::BN;
-        for (int sw = 0; sw < a.nsweeps && ok; ++sw) {
-          const Sweep S = sched[sw];
-          const int np = S.nplanes;
-          for (int kc = S.k0c; kc < S.k1c; kc += S.kcs, ++it) {
-            const int nu = S.k1c - kc < S.kcs ? S.k1c - kc : S.kcs;
-            const int st = (int)(it % stages);
-            const uint32_t par = (uint32_t)((it / stages) & 1) ^ 1u;
-            if (aborted(abortp) || !mbar_wait(&stage_empty[st], par, a.wait_limit)) {
-              if (!aborted(abortp)) raise_timeout(a, abortp);
-              ok = false;
-              break;
-            }
-            uint8_t* base = smem + (size_t)st * stage_bytes;
-            mbar_arrive_expect_tx(&stage_full[st], (uint32_t)(nu * np) * (Cf::A_TILE + Cf::B_TILE));
-            for (int u = 0; u < nu; ++u)
-              for (int p = 0; p < np; ++p) {
-                const int t = u * np + p;
-                tma_load_3d(base + t * Cf::A_TILE, &tmA, &stage_full[st], (kc + u) * kBK, m0, p);
-                tma_load_3d(base + s * Cf::A_TILE + t * Cf::B_TILE, &tmB, &stage_full[st], (kc + u) * kBK, n0, p);
-              }
+    }
+    __syncwarp();
+    long it = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+      int tm, tn;
+      tile_coords(a, tile, tm, tn);
+      const int m0 = tm * Cf::BM, n0 = tn * Cf::BN;
+      for (int sw = 0; sw < a.nsweeps && ok; ++sw) {
+        const Sweep S = sched[sw];
+        const int np = S.nplanes;
+        for (int kc = S.k0c; kc < S.k1c; kc += S.kcs, ++it) {
+          const int nu = S.k1c - kc < S.kcs ? S.k1c - kc : S.kcs;
+          const int st = (int)(it % stages);
+          const uint32_t par = (uint32_t)((it / stages) & 1) ^ 1u;
+          if (aborted(abortp) || !mbar_wait_warp(&stage_empty[st], par, a.wait_limit)) {
+            if (!aborted(abortp) && lane == 0) raise_timeout(a, abortp);
+            ok = false;
+            break;
           }
+          uint8_t* base = smem + (size_t)st * stage_bytes;
+          mbar_arrive_expect_tx_elect(&stage_full[st], (uint32_t)(nu * np) * (Cf::A_TILE + Cf::B_TILE));
+          for (int u = 0; u < nu; ++u)
+            for (int p = 0; p < np; ++p) {
+              const int t = u * np + p;
+              tma_load_3d_elect(base + t * Cf::A_TILE, &tmA, &stage_full[st], (kc + u) * kBK, m0, p);
+              tma_load_3d_elect(base + s * Cf::A_TILE + t * Cf::B_TILE, &tmB, &stage_full[st], (kc + u) * kBK, n0,
+                                p);
+            }
         }
       }
-      if (!ok) {
-        // wait (bounded) for the copies still in flight before the block exits
-        for (long j = (it - stages > 0 ? it - stages : 0); j < it; ++j)
-          mbar_wait(&stage_full[j % stages], (uint32_t)((j / stages) & 1), a.wait_limit / 8);
-      }
+    }
+    if (!ok) {
+      // wait (bounded) for the copies still in flight before the block exits
+      for (long j = (it - stages > 0 ? it - stages : 0); j < it; ++j)
+        mbar_wait(&stage_full[j % stages], (uint32_t)((j / stages) & 1), a.wait_limit / 8);
     }
   } else if (warp >= 1 && warp <= kMmaWarps) {
     // ------------------------------------------------------------ MMA issuers
+    // the whole warp runs the loop (warp-uniform values); one elected lane issues
     const int myj = warp - 1;   // job of each sweep issued by this warp
-    if (lane == 0) {
+    {
       constexpr uint32_t idesc = idesc_bf16_f32(128, Cf::BN);
       long it = 0, tloc = 0;
       bool ok = true;
@@ -247,8 +251,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t e = srow[jj + myj];
             slot = (int)(e & 3u);
             dcol = tmem + (uint32_t)(slot * Cf::BN);
-            if (aborted(abortp) || !mbar_wait(&slot_empty[slot], ((e >> 2) & 1u) ^ 1u, a.wait_limit)) {
-              if (!aborted(abortp)) raise_timeout(a, abortp);
+            if (aborted(abortp) || !mbar_wait_warp(&slot_empty[slot], ((e >> 2) & 1u) ^ 1u, a.wait_limit)) {
+              if (!aborted(abortp) && lane == 0) raise_timeout(a, abortp);
               ok = false;
               break;
             }
@@ -258,8 +262,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int kc = S.k0c; kc < S.k1c; kc += S.kcs, ++it) {
             const int nu = S.k1c - kc < S.kcs ? S.k1c - kc : S.kcs;
             const int st = (int)(it % stages);
-            if (aborted(abortp) || !mbar_wait(&stage_full[st], (uint32_t)((it / stages) & 1), a.wait_limit)) {
-              if (!aborted(abortp)) raise_timeout(a, abortp);
+            if (aborted(abortp) || !mbar_wait_warp(&stage_full[st], (uint32_t)((it / stages) & 1), a.wait_limit)) {
+              if (!aborted(abortp) && lane == 0) raise_timeout(a, abortp);
               ok = false;
               break;
             }
@@ -282,19 +286,19 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int kk = 0; kk < kBK / 16; ++kk) {
                   const uint32_t acc = (!first || p != pb || kk != 0) ? 1u : 0u;
-                  mma_bf16(dcol, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, acc);
+                  mma_bf16_elect(dcol, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, acc);
                 }
               }
             }
-            mma_commit(&stage_empty[st]);   // also by a warp without a job here: the stage needs both
+            mma_commit_elect(&stage_empty[st]);   // also by a warp without a job here: the stage needs both
           }
           if (!ok) break;
-          if (mine) mma_commit(&slot_full[slot]);
+          if (mine) mma_commit_elect(&slot_full[slot]);
           jj += nj;
         }
       }
-      // every MMA issued by this thread must be complete before TMEM is released
-      mma_commit(&mma_done[myj]);
+      // every MMA issued by this warp must be complete before TMEM is released
+      mma_commit_elect(&mma_done[myj]);
       mbar_wait(&mma_done[myj], 0, a.wait_limit);
     }
   }

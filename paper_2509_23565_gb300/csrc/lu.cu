@@ -1358,24 +1358,32 @@ int emul_dpotrf(emul_handle_t h, char uplo, int n, double* A, int lda, int nb, i
   const emul::LuBufs B = emul::carve(h, gw, nb);
   for (int j0 = 0; j0 < n; j0 += nb) {
     const int jb = nb < n - j0 ? nb : n - j0;
+    const int m2 = n - j0 - jb;
+    int ph = emul::phase_begin(h, EMUL_PHASE_PANEL);
     emul::potf2_kernel<<<1, 256, 0, h->stream>>>(A, lda, j0, jb, info);
     h->launches++;
     rc = emul::check_cuda(h, cudaGetLastError(), "potf2");
     if (rc) return rc;
-    const int m2 = n - j0 - jb;
     if (m2 > 0) {
       emul::trtri_lower_kernel<<<jb, (jb + 31) / 32 * 32, jb * sizeof(double), h->stream>>>(A, lda, j0, jb, 0, B.inv);
       h->launches++;
       rc = emul::check_cuda(h, cudaGetLastError(), "trtri");
       if (rc) return rc;
+    }
+    emul::phase_end(h, ph);
+    if (m2 > 0) {
       double* A21 = A + (j0 + jb) + static_cast<long>(j0) * lda;
       // L21 = A21 L11^-T: operand B is (L11^-1)^T, whose row j is row j of L11^-1
+      ph = emul::phase_begin(h, EMUL_PHASE_U12);
       rc = emul::gemm_run(h, m2, jb, jb, 1.0, Operand{A21, 1, lda}, Operand{B.inv, 1, jb}, 0.0, A21, lda, slices,
                           false, 0, nullptr, 0, 0);
+      emul::phase_end(h, ph);
       if (rc) return rc;
       // A22 -= L21 L21^T on the lower triangle; one slice set for both operands
+      ph = emul::phase_begin(h, EMUL_PHASE_UPDATE);
       rc = emul::gemm_run(h, m2, m2, jb, -1.0, Operand{A21, 1, lda}, Operand{A21, 1, lda}, 1.0,
                           A + (j0 + jb) + static_cast<long>(j0 + jb) * lda, lda, slices, true, 0, nullptr, 0, 0);
+      emul::phase_end(h, ph);
       if (rc) return rc;
     }
     if (stats) stats->steps++;
@@ -1390,6 +1398,7 @@ int emul_dpotrs(emul_handle_t h, char uplo, int n, int nrhs, const double* L, in
       (n > 0 && nrhs > 0 && (!L || !B)))
     return emul::set_error(h, EMUL_INVALID_ARG, "emul_dpotrs: invalid argument");
   if (n == 0 || nrhs == 0) return EMUL_OK;
+  const int ph = emul::phase_begin(h, EMUL_PHASE_SOLVE);
   constexpr int bs = 128;
   for (int d0 = 0; d0 < n; d0 += bs) {
     const int b = bs < n - d0 ? bs : n - d0;
@@ -1406,6 +1415,7 @@ int emul_dpotrs(emul_handle_t h, char uplo, int n, int nrhs, const double* L, in
     if (d0 > 0)
       emul::gemv_update_kernel<<<dim3((d0 + 7) / 8, nrhs), 256, 0, h->stream>>>(L, lda, B, ldb, 0, d0, d0, b, 1);
   }
+  emul::phase_end(h, ph);
   return emul::check_cuda(h, cudaGetLastError(), "potrs");
 }
 

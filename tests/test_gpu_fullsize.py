@@ -95,7 +95,11 @@ def test_cholesky_16384_cond1e12_s7(gpu_lib):
     berr = residual.backward_error(A, x, b)
     eq8 = residual.scaled_residual(A, x, b)
     assert berr < 16 and eq8 < 16, (berr, eq8)
-    assert abs(dev[1] - berr) <= 1e-9 * max(1.0, berr)
+    # x is of order 1e12 here, so A x - b cancels to about 1e-12 of |A||x|: the
+    # device kernel and numpy sum the products of A x in different orders and
+    # agree only to the rounding of A x, which in these units (||A|| ||x|| n eps)
+    # is about 1 / sqrt(n) for random rounding errors
+    assert abs(dev[1] - berr) <= 1e-2, (dev[1], berr)
     L = dA.numpy()
     # the strictly upper triangle is not touched
     assert np.array_equal(np.triu(L, 1), np.triu(A, 1))
