@@ -10,15 +10,20 @@
 // splits K where needed), so the FP32 sums are exact.  The epilogue converts
 // each drained level exactly to an integer and folds it into a Horner state
 // R = R * 2^7 + I_L (int64, or 128-bit for the wide variant); the final value
-// T = sum_L I_L 2^(7(t-L)) is rounded once to FP64 in integer arithmetic,
+// T = sum_L I_L 2^(7(t-L)) is rounded once to FP64,
 //   D = RN(T * 2^(e_i + f_j - 7t)),
-// and C = RN(RN(alpha D) + RN(beta C)) is written straight back.
+// from two exact parts with one FP64 add, and C = RN(RN(alpha D) + RN(beta C))
+// is written straight back.  For the Schur update (alpha = -1, beta = 1) the
+// epilogue does not read C: it issues red.global.add.f64 of -D, an FP64 add
+// rounded to nearest that L2 performs, so the C update costs no load latency
+// and no FP64 instruction on the SM (GB300 retires ~1.6 per clock per SM).
 //
 // Warp roles (640 threads): warp 0 issues TMA loads of the slice tiles of each
 // K chunk into a ring of shared-memory stages; warp 1 owns TMEM (4 accumulator
-// slots); warps 1 and 2 issue the MMAs, one job of a sweep each (one issuing
-// thread cannot keep the tensor core busy with 128 x 128 x 16 MMAs); warps 4-19
-// drain the slots and write C.  The
+// slots); warps 1 and 2 issue the MMAs, one job of a sweep each; both loops run
+// on the whole warp (warp-uniform operands, one elected lane issues: a lone
+// thread recomputing descriptors issues an MMA only every ~84 cycles, short of
+// the 64 a 128 x 128 x 16 MMA takes); warps 4-19 drain the slots and write C.  The
 // first warpgroup gives registers to the epilogue warpgroups (setmaxnreg).  A sweep
 // of one or two jobs shares the staged tiles of a chunk; each job's TMEM slot
 // (and the parity of its barriers) comes from a host-planned slot table, so the
@@ -82,15 +87,19 @@ __device__ __forceinline__ double rn_split(long long R, int I, int sh) {
   return __dadd_rn(dh, dl);
 }
 
+// C <- RN(C + v) as a reduction in L2 (fire and forget: no load of C, no FP64
+// instruction on the SM).  The FP64 add of red.global rounds to nearest even;
+// each element of C is updated by exactly one thread of one launch.
+__device__ __forceinline__ void red_add_f64(double* p, double v) {
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
 __device__ __forceinline__ int f2i(uint32_t r) { return __float2int_rn(__uint_as_float(r)); }
 
 __device__ __forceinline__ double neg_d(double x) {
   return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
 }
 
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
 
 // D = RN(T * 2^(e + f - 7t)) (NaN for a non-finite scale), then
 // out = RN(RN(alpha D) + RN(beta C)); alpha = +-1 and beta in {0, 1} skip the
@@ -328,12 +337,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int col = col0 + lane;
         fcol[0] = (lane < CPT && col < a.N) ? a.fb[col] : 0;
       }
-      // pull this thread's C entries into L2 while the products run
-      if (needs_c && a.mode == 0 && row < a.M) {
-#pragma unroll 4
-        for (int c = 0; c < CPT; ++c)
-          if (col0 + c < a.N) prefetch_l2(a.C + row + (long)(col0 + c) * a.ldc);
-      }
 #pragma unroll
       for (int c = 0; c < CPT; ++c) R[c] = 0;
       const uint8_t* srow = slot_row(tab, a.slots, tloc);
@@ -392,12 +395,6 @@ __global__ void __launch_bounds__(kThreads, 1)
               uint32_t r0[4], r1[4];
               tmem_ld4(ta + c4 * 4, r0);
               if (take) tmem_ld4(tb + c4 * 4, r1);
-              double cv[4];
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                const int col = col0 + c4 * 4 + q;
-                cv[q] = (needs_c && rowok && col < a.N) ? a.C[row + (long)col * a.ldc] : 0.0;
-              }
               tmem_ld_wait();
 #pragma unroll
               for (int q = 0; q < 4; ++q) {
@@ -413,7 +410,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                   D = rn_scaled((__int128)R[c] * 128 + (__int128)I, e_row + f + sh0);
                 else
                   D = rn_split((long long)R[c], I, e_row + f + sh0);
-                a.C[row + (long)col * a.ldc] = apply_update<UPD>(a, D, cv[q]);
+                double* cp = a.C + row + (long)col * a.ldc;
+                if (UPD == kSub)
+                  red_add_f64(cp, neg_d(D));
+                else if (UPD == kSet)
+                  *cp = D;
+                else
+                  *cp = apply_update<UPD>(a, D, needs_c ? *cp : 0.0);
               }
             }
           } else {
@@ -452,28 +455,24 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       if (ok && a.mode == 0 && !final_done) {
         // every level was folded into R (wide variant): T = R
+        const bool rowok = row < a.M;
 #pragma unroll
-        for (int c8 = 0; c8 < CPT / 8; ++c8) {
-          double cv[8];
-          const bool rowok = row < a.M;
-#pragma unroll
-          for (int jj = 0; jj < 8; ++jj) {
-            const int col = col0 + c8 * 8 + jj;
-            cv[jj] = (needs_c && rowok && col < a.N) ? a.C[row + (long)col * a.ldc] : 0.0;
-          }
-#pragma unroll
-          for (int jj = 0; jj < 8; ++jj) {
-            const int c = c8 * 8 + jj;
-            const int col = col0 + c;
-            const int f = __shfl_sync(0xFFFFFFFFu, fcol[0], c);
-            if (!rowok || col >= a.N || (a.lower && row < col)) continue;
-            double D;
-            if (e_row == kNonFinite || f == kNonFinite)
-              D = __longlong_as_double(0x7FF8000000000000ll);
-            else
-              D = rn_scaled((__int128)R[c], e_row + f + sh0);
-            a.C[row + (long)col * a.ldc] = apply_update<UPD>(a, D, cv[jj]);
-          }
+        for (int c = 0; c < CPT; ++c) {
+          const int col = col0 + c;
+          const int f = __shfl_sync(0xFFFFFFFFu, fcol[0], c);
+          if (!rowok || col >= a.N || (a.lower && row < col)) continue;
+          double D;
+          if (e_row == kNonFinite || f == kNonFinite)
+            D = __longlong_as_double(0x7FF8000000000000ll);
+          else
+            D = rn_scaled((__int128)R[c], e_row + f + sh0);
+          double* cp = a.C + row + (long)col * a.ldc;
+          if (UPD == kSub)
+            red_add_f64(cp, neg_d(D));
+          else if (UPD == kSet)
+            *cp = D;
+          else
+            *cp = apply_update<UPD>(a, D, needs_c ? *cp : 0.0);
         }
       }
     }
