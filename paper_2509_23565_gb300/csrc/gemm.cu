@@ -87,6 +87,37 @@ __device__ __forceinline__ double rn_split(long long R, int I, int sh) {
   return __dadd_rn(dh, dl);
 }
 
+// RN(x * 2^sh) for a 64-bit integer x, in integer arithmetic only, valid for
+// -1022 <= sh <= 960 (every |x| < 2^63 then gives a normal result or, after a
+// carry, the largest binade): the magnitude is cut to 53 bits with ties to
+// even; a carry out of the mantissa moves into the exponent field.
+__device__ __forceinline__ double rn_x64(long long x, int sh) {
+  if (x == 0) return 0.0;
+  const unsigned long long sign = x < 0 ? 0x8000000000000000ull : 0ull;
+  const unsigned long long a = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
+  const int msb = 63 - __clzll((long long)a);
+  unsigned long long q;
+  if (msb <= 52) {
+    q = a << (52 - msb);
+  } else {
+    const int r = msb - 52;
+    q = a >> r;
+    const unsigned long long rem = a & ((1ull << r) - 1ull), half = 1ull << (r - 1);
+    q += (rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull;
+  }
+  return __longlong_as_double((long long)(sign | (((unsigned long long)(msb + sh + 1022) << 52) + q)));
+}
+
+// RN(T * 2^sh) for T = R * 2^7 + I: with |R| < 2^55 (the usual case: the
+// Horner state reaches 2^57 only when the leading digits of whole rows and
+// columns are near 127 with one sign) T fits in 64 bits and is rounded with
+// integer operations alone; otherwise the two-part path with one FP64 add.
+__device__ __forceinline__ double rn_final(long long R, int I, int sh) {
+  const long long lim = 1ll << 55;
+  if (R > -lim && R < lim && sh >= -1022 && sh <= 960) return rn_x64((R << 7) + I, sh);
+  return rn_split(R, I, sh);
+}
+
 // C <- RN(C + v) as a reduction in L2 (fire and forget: no load of C, no FP64
 // instruction on the SM).  The FP64 add of red.global rounds to nearest even;
 // each element of C is updated by exactly one thread of one launch.
@@ -409,7 +440,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 else if (WIDE)
                   D = rn_scaled((__int128)R[c] * 128 + (__int128)I, e_row + f + sh0);
                 else
-                  D = rn_split((long long)R[c], I, e_row + f + sh0);
+                  D = rn_final((long long)R[c], I, e_row + f + sh0);
                 double* cp = a.C + row + (long)col * a.ldc;
                 if (UPD == kSub)
                   red_add_f64(cp, neg_d(D));

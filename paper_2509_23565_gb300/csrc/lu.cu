@@ -522,57 +522,182 @@ __global__ void __launch_bounds__(256) trsm_small_kernel(double* A, long lda, in
     if (lane + 32 * t < w1) col[lane + 32 * t] = x[t];
 }
 
-// inv (nb x nb, ld nb) <- L^-1 for L = the nb x nb lower triangle at A[d0.., d0..]
-// (unit diagonal if `unit`).  One block per column of the inverse.
-__global__ void trtri_lower_kernel(const double* A, long lda, int d0, int nb, int unit, double* inv) {
-  extern __shared__ double xs[];
-  const int j = blockIdx.x, i = threadIdx.x;
-  const double* L = A + d0 + static_cast<long>(d0) * lda;
-  if (i < nb) xs[i] = (i == j) ? 1.0 : 0.0;
-  __syncthreads();
-  for (int k = j; k < nb; ++k) {
-    if (!unit) {
-      if (i == k) xs[k] = xs[k] / L[k + static_cast<long>(k) * lda];
-      __syncthreads();
-    }
-    const double xk = xs[k];
-    if (i > k && i < nb) xs[i] = fma(-L[i + static_cast<long>(k) * lda], xk, xs[i]);
-    __syncthreads();
-  }
-  if (i < nb) inv[i + static_cast<long>(j) * nb] = (i < j) ? 0.0 : xs[i];
-}
+// ---------------------------------------------------------------- Cholesky diagonal block
+// The nb x nb diagonal block of a Cholesky step (nb <= 256) is factored in
+// FP64 by 32-column panels: a one-block leaf factors the panel's 32 x 32
+// diagonal block in shared memory, the rows below it within the block are
+// solved against it and the rest of the block is updated by a small FP64
+// product spread over many blocks, and L11^-1 is formed afterwards column by
+// column.  GB300 retires ~1.6 FP64 instructions per clock per SM, so no step
+// keeps a large amount of FP64 work on a single SM.
+constexpr int kCholLeaf = 32;
 
-// Unblocked lower Cholesky of the nb x nb diagonal block at A[d0.., d0..] (one block).
-__global__ void potf2_kernel(double* A, long lda, int d0, int nb, int32_t* info) {
-  double* D = A + d0 + static_cast<long>(d0) * lda;
-  __shared__ double djj;
+// Unblocked lower Cholesky of the w x w (w <= 32) block at A[d0.., d0..] in
+// shared memory, right-looking: pivot sqrt, column scaled by its reciprocal,
+// rank-1 update of the trailing lower triangle.  A non-positive pivot sets
+// *info (first index) and stops; nothing runs once *info is set.
+// It also writes the leaf's own inverse L^-1 (lower, w x w) to inv[i + j*ldi]
+// for the solve of the rows below it.
+__global__ void __launch_bounds__(256) chol_leaf_kernel(double* A, long lda, int d0, int w, double* inv, int ldi,
+                                                       int32_t* info) {
+  __shared__ double D[kCholLeaf][kCholLeaf + 1];
   __shared__ int fail;
-  const int i = threadIdx.x;
-  if (i == 0) fail = (*info != 0);
+  const int t = threadIdx.x;
+  if (t == 0) fail = (*info != 0);
   __syncthreads();
   if (fail) return;
-  for (int j = 0; j < nb; ++j) {
-    if (i == 0) {
-      const double d = D[j + static_cast<long>(j) * lda];
+  double* blk = A + d0 + static_cast<long>(d0) * lda;
+  for (int e = t; e < w * w; e += blockDim.x) {
+    const int i = e % w, j = e / w;
+    if (i >= j) D[i][j] = blk[i + static_cast<long>(j) * lda];
+  }
+  __syncthreads();
+  int done = w;
+  for (int j = 0; j < w; ++j) {
+    if (t == 0) {
+      const double d = D[j][j];
       if (!(d > 0.0)) {
         atomicCAS(info, 0, d0 + j + 1);
         fail = 1;
       } else {
-        djj = sqrt(d);
-        D[j + static_cast<long>(j) * lda] = djj;
+        D[j][j] = sqrt(d);
       }
     }
     __syncthreads();
-    if (fail) return;
-    const double r = 1.0 / djj;
-    for (int ii = j + 1 + i; ii < nb; ii += blockDim.x) D[ii + static_cast<long>(j) * lda] *= r;
+    if (fail) {
+      done = j;
+      break;
+    }
+    const double r = 1.0 / D[j][j];
+    if (t > j && t < w) D[t][j] *= r;
     __syncthreads();
-    for (int ii = j + 1 + i; ii < nb; ii += blockDim.x) {
-      const double lij = D[ii + static_cast<long>(j) * lda];
-      for (int kk = j + 1; kk <= ii; ++kk)
-        D[ii + static_cast<long>(kk) * lda] = fma(-lij, D[kk + static_cast<long>(j) * lda], D[ii + static_cast<long>(kk) * lda]);
+    // D[i][k] -= D[i][j] D[k][j] for j < k <= i < w
+    const int m = w - 1 - j;   // trailing size
+    for (int e = t; e < m * m; e += blockDim.x) {
+      const int i = j + 1 + e % m, k = j + 1 + e / m;
+      if (k <= i) D[i][k] = fma(-D[i][j], D[k][j], D[i][k]);
     }
     __syncthreads();
+  }
+  // write back the columns that were finished (all of them unless a pivot failed)
+  for (int e = t; e < w * w; e += blockDim.x) {
+    const int i = e % w, j = e / w;
+    if (i >= j && j < done) blk[i + static_cast<long>(j) * lda] = D[i][j];
+  }
+  if (done < w) return;
+  // inverse: thread j solves L x = e_j by forward substitution (x_i for i < j are 0)
+  if (t < w) {
+    const int j = t;
+    double xs[kCholLeaf];
+#pragma unroll
+    for (int i = 0; i < kCholLeaf; ++i) {
+      if (i < j || i >= w) {
+        xs[i] = 0.0;
+        continue;
+      }
+      double acc = (i == j) ? 1.0 : 0.0;
+#pragma unroll
+      for (int k = 0; k < kCholLeaf; ++k)
+        if (k >= j && k < i) acc = fma(-D[i][k], xs[k], acc);
+      xs[i] = acc / D[i][i];
+    }
+#pragma unroll
+    for (int i = 0; i < kCholLeaf; ++i)
+      if (i < w) inv[i + static_cast<long>(j) * ldi] = xs[i];
+  }
+}
+
+// C(i, j) = beta C(i, j) + alpha sum_l A(i, l) B(j, l) in FP64, for the m x n
+// C (ldc) with A(i, l) = A[i*ars + l*acs] and B(j, l) = B[j*brs + l*bcs];
+// lower = 1 writes only i >= j.  A block computes a 16 x 32 tile (one entry
+// per thread) over K chunks of 32 staged in shared memory; with n <= 32 and
+// k <= 32 every block reads all its operands before it writes, so C may then
+// alias A's rows of the same block (the in-place triangular solve).
+__global__ void __launch_bounds__(512) dgemm_nt_small_kernel(int m, int n, int k, double alpha, const double* A,
+                                                            long ars, long acs, const double* B, long brs,
+                                                            long bcs, double beta, double* C, long ldc,
+                                                            int lower, const int32_t* info) {
+  __shared__ double As[16][33], Bs[32][33];
+  if (*info != 0) return;
+  const int ti = threadIdx.x & 15, tj = threadIdx.x >> 4;
+  const int i0 = blockIdx.x * 16, j0 = blockIdx.y * 32;
+  if (lower && j0 > i0 + 15) return;          // tile entirely above the diagonal
+  const int i = i0 + ti, j = j0 + tj;
+  double acc = 0.0;
+  for (int l0 = 0; l0 < k; l0 += 32) {
+    for (int e = threadIdx.x; e < 16 * 32; e += blockDim.x) {
+      const int r = e & 15, l = e >> 4;
+      As[r][l] = (i0 + r < m && l0 + l < k) ? A[(i0 + r) * ars + static_cast<long>(l0 + l) * acs] : 0.0;
+    }
+    for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+      const int r = e & 31, l = e >> 5;
+      Bs[r][l] = (j0 + r < n && l0 + l < k) ? B[(j0 + r) * brs + static_cast<long>(l0 + l) * bcs] : 0.0;
+    }
+    __syncthreads();
+    const int lk = k - l0 < 32 ? k - l0 : 32;
+    for (int l = 0; l < lk; ++l) acc = fma(As[ti][l], Bs[tj][l], acc);
+    __syncthreads();
+  }
+  if (i < m && j < n && (!lower || i >= j)) {
+    double* c = C + i + static_cast<long>(j) * ldc;
+    *c = beta == 0.0 ? alpha * acc : fma(alpha, acc, beta * *c);
+  }
+}
+
+// inv (nb x nb, ld nb) <- L^-1 for the lower triangular L at A[d0.., d0..]
+// (unit diagonal if `unit`; nb <= 256): each block solves L x = e_j for the two
+// columns j and nb - 1 - j (balanced work) by column substitution.  Thread i
+// owns row i of both x's in registers and reads row i of L sixteen columns
+// ahead (coalesced along the column); x_k is published through shared
+// memory, one barrier per step.
+__global__ void __launch_bounds__(256) trtri_cols_kernel(const double* A, long lda, int d0, int nb, int unit,
+                                                        double* inv, const int32_t* info) {
+  __shared__ double bc[2][2];
+  if (info && *info != 0) return;
+  const double* L = A + d0 + static_cast<long>(d0) * lda;
+  const int i = threadIdx.x;
+  const int j0 = blockIdx.x, j1 = nb - 1 - static_cast<int>(blockIdx.x);
+  double x0 = (i == j0) ? 1.0 : 0.0, x1 = (i == j1) ? 1.0 : 0.0;
+  double ln[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int kk = j0 + q;
+    ln[q] = (i < nb && kk < nb && i >= kk + unit) ? L[i + static_cast<long>(kk) * lda] : 0.0;
+  }
+  for (int g = j0; g < nb; g += 16) {
+    double lv[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) lv[q] = ln[q];
+    if (g + 16 < nb) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int kk = g + 16 + q;
+        ln[q] = (i < nb && kk < nb && i >= kk + unit) ? L[i + static_cast<long>(kk) * lda] : 0.0;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int kk = g + q;
+      if (kk >= nb) break;
+      if (i == kk) {
+        if (!unit) {
+          x0 = x0 / lv[q];
+          x1 = x1 / lv[q];
+        }
+        bc[kk & 1][0] = x0;
+        bc[kk & 1][1] = x1;
+      }
+      __syncthreads();
+      const double b0 = bc[kk & 1][0], b1 = bc[kk & 1][1];
+      if (i > kk && i < nb) {
+        x0 = fma(-lv[q], b0, x0);
+        x1 = fma(-lv[q], b1, x1);
+      }
+    }
+  }
+  if (i < nb) {
+    inv[i + static_cast<long>(j0) * nb] = x0;
+    inv[i + static_cast<long>(j1) * nb] = x1;
   }
 }
 
@@ -816,6 +941,37 @@ size_t lu_extra_bytes(int nb, int nsm) {
   return al(static_cast<size_t>(nb) * nb * 8) + al(rec_bytes(nsm)) + al(2ull * 2 * kLeaf * 8) + al(4 * 8) +
          al(kMaxDepth * kMapInts * 4) +
          al((4ull * kProbeRows + 2ull * nb) * 8) + al(16) + kAl;
+}
+
+// Lower Cholesky of the jb x jb diagonal block at A[d0.., d0..] (jb <= 256),
+// in place, by 32-column panels (chol_leaf_kernel, then the rows below the
+// leaf within the block and the block's trailing lower part by
+// dgemm_nt_small_kernel); with `want_inv`, inv (jb x jb, ld jb) <- L11^-1.
+int chol_diag(emul_handle_t h, double* A, long lda, int d0, int jb, double* inv, int32_t* info, bool want_inv) {
+  for (int c0 = 0; c0 < jb; c0 += kCholLeaf) {
+    const int wp = kCholLeaf < jb - c0 ? kCholLeaf : jb - c0;
+    chol_leaf_kernel<<<1, 256, 0, h->stream>>>(A, lda, d0 + c0, wp, inv + c0 + static_cast<long>(c0) * jb, jb,
+                                               info);
+    h->launches++;
+    const int r0 = c0 + wp, mr = jb - r0;
+    if (mr > 0) {
+      double* Lp = A + (d0 + r0) + static_cast<long>(d0 + c0) * lda;   // rows below the leaf, its columns
+      const double* ip = inv + c0 + static_cast<long>(c0) * jb;       // the leaf's inverse
+      // L(r0.., c0..) = A(r0.., c0..) L_pp^-T, in place (n = k = wp <= 32)
+      dgemm_nt_small_kernel<<<dim3((mr + 15) / 16, 1), 512, 0, h->stream>>>(mr, wp, wp, 1.0, Lp, 1, lda, ip, 1, jb,
+                                                                          0.0, Lp, lda, 0, info);
+      // A(r0.., r0..) -= L(r0.., c0..) L(r0.., c0..)^T, lower part
+      dgemm_nt_small_kernel<<<dim3((mr + 15) / 16, (mr + 31) / 32), 512, 0, h->stream>>>(
+          mr, mr, wp, -1.0, Lp, 1, lda, Lp, 1, lda, 1.0, A + (d0 + r0) + static_cast<long>(d0 + r0) * lda, lda, 1,
+          info);
+      h->launches += 2;
+    }
+  }
+  if (want_inv) {
+    trtri_cols_kernel<<<(jb + 1) / 2, 256, 0, h->stream>>>(A, lda, d0, jb, 0, inv, info);
+    h->launches++;
+  }
+  return check_cuda(h, cudaGetLastError(), "Cholesky diagonal block");
 }
 
 LuBufs carve(emul_handle_t h, size_t off, int nb) {
@@ -1215,7 +1371,7 @@ int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int n
     const int m2 = n - j0 - jb;
     if (m2 > 0) {
       ph = emul::phase_begin(h, EMUL_PHASE_U12);
-      emul::trtri_lower_kernel<<<jb, (jb + 31) / 32 * 32, jb * sizeof(double), h->stream>>>(A, lda, j0, jb, 1, B.inv);
+      emul::trtri_cols_kernel<<<(jb + 1) / 2, 256, 0, h->stream>>>(A, lda, j0, jb, 1, B.inv, nullptr);
       h->launches++;
       rc = emul::check_cuda(h, cudaGetLastError(), "trtri");
       if (rc) return rc;
@@ -1360,17 +1516,9 @@ int emul_dpotrf(emul_handle_t h, char uplo, int n, double* A, int lda, int nb, i
     const int jb = nb < n - j0 ? nb : n - j0;
     const int m2 = n - j0 - jb;
     int ph = emul::phase_begin(h, EMUL_PHASE_PANEL);
-    emul::potf2_kernel<<<1, 256, 0, h->stream>>>(A, lda, j0, jb, info);
-    h->launches++;
-    rc = emul::check_cuda(h, cudaGetLastError(), "potf2");
-    if (rc) return rc;
-    if (m2 > 0) {
-      emul::trtri_lower_kernel<<<jb, (jb + 31) / 32 * 32, jb * sizeof(double), h->stream>>>(A, lda, j0, jb, 0, B.inv);
-      h->launches++;
-      rc = emul::check_cuda(h, cudaGetLastError(), "trtri");
-      if (rc) return rc;
-    }
+    rc = emul::chol_diag(h, A, lda, j0, jb, B.inv, info, m2 > 0);
     emul::phase_end(h, ph);
+    if (rc) return rc;
     if (m2 > 0) {
       double* A21 = A + (j0 + jb) + static_cast<long>(j0) * lda;
       // L21 = A21 L11^-T: operand B is (L11^-1)^T, whose row j is row j of L11^-1

@@ -111,6 +111,26 @@ def test_dgemm_bitexact(gpu_lib, m, n, k, s, alpha, beta):
     assert _same_bits(got, want), np.nanmax(np.abs(got - want))
 
 
+@pytest.mark.parametrize("s,k", [(7, 256), (7, 200), (6, 256), (5, 128), (8, 256)])
+def test_dgemm_large_horner_state(gpu_lib, s, k):
+    """Rows and columns whose digits are all near 127 with one sign drive the
+    exact sum T to its largest magnitude (beyond 2^64 at s = 7, k = 256), which
+    the epilogue rounds on its wide path; other rows are random, so one warp
+    mixes both paths.  Bit for bit against the oracle, C - A B form."""
+    m, n = 200, 170
+    A = inputs.uniform(m, k, seed=31 + k)
+    B = inputs.uniform(k, n, seed=32 + k)
+    A[::3, :] = 1.0 - 2.0**-53                 # every third row: all digits 127
+    B[:, ::2] = -(1.0 - 2.0**-53)              # every second column: all digits 127, other sign
+    A[7, :] = -(1.0 - 2.0**-53)
+    C = inputs.uniform(m, n, seed=33)
+    dC = ColMajor.from_numpy(C)
+    gpu_lib.dgemm(ColMajor.from_numpy(A), ColMajor.from_numpy(B), dC, s, -1.0, 1.0)
+    gpu_lib.sync_status()
+    want = emulgemm.emul_gemm(A, B, s, alpha=-1.0, beta=1.0, C=C)
+    assert _same_bits(dC.numpy(), want)
+
+
 def test_dgemm_special_values(gpu_lib):
     m, n, k = 70, 40, 50
     A = _special_matrix(m, k, 5)

@@ -148,7 +148,8 @@ def test_multiple_rhs(gpu_lib):
         assert residual.backward_error(A, X[:, j], B[:, j]) < 16
 
 
-@pytest.mark.parametrize("n,nb,cond", [(130, 32, 1e2), (512, 64, 1e8), (1000, 128, 1e12)])
+@pytest.mark.parametrize("n,nb,cond", [(130, 32, 1e2), (512, 64, 1e8), (1000, 128, 1e12), (1000, 256, 1e8),
+                                       (333, 48, 1e4)])
 @pytest.mark.parametrize("s", [7, 8])
 def test_potrf_potrs(gpu_lib, n, nb, cond, s):
     A = inputs.spd(n, cond, seed=70 + n)
@@ -167,12 +168,16 @@ def test_potrf_potrs(gpu_lib, n, nb, cond, s):
     assert residual.backward_error(A, x, b) < 16
 
 
-def test_potrf_not_spd(gpu_lib):
-    A = inputs.spd(200, 10.0, seed=80)
-    A[150, 150] = -5.0
+@pytest.mark.parametrize("nb,at", [(32, 150), (256, 300), (256, 45)])
+def test_potrf_not_spd(gpu_lib, nb, at):
+    """A negative diagonal entry makes the leading minor of that order
+    non-positive; info is its 1-based index wherever it falls in the blocks
+    and 32-column panels of the diagonal block."""
+    A = inputs.spd(400, 10.0, seed=80)
+    A[at, at] = -5.0
     dA = ColMajor.from_numpy(A)
-    info = gpu_lib.dpotrf(dA, nb=32, slices=7)
-    assert int(info.item()) == 151
+    info = gpu_lib.dpotrf(dA, nb=nb, slices=7)
+    assert int(info.item()) == at + 1
 
 
 @pytest.mark.parametrize("n", [4096])
