@@ -241,8 +241,10 @@ def run_ours(args, world, rank, local):
     flops = chol_flops if chol else lu_flops
     seed = 7000 + rank
     A_host = None
-    if chol:
-        A0 = inputs.spd_device(n, args.cond, seed=seed)              # symmetric: store = matrix
+    if chol and n <= 8192:
+        A0 = torch.from_numpy(inputs.spd(n, args.cond, seed=seed)).cuda()   # symmetric: store = matrix
+    elif chol:
+        A0 = inputs.spd_device(n, args.cond, seed=seed)
     elif args.range > 0:
         gen = torch.Generator(device="cuda")
         gen.manual_seed(seed)

@@ -533,78 +533,74 @@ __global__ void __launch_bounds__(256) trsm_small_kernel(double* A, long lda, in
 constexpr int kCholLeaf = 32;
 
 // Unblocked lower Cholesky of the w x w (w <= 32) block at A[d0.., d0..] in
-// shared memory, right-looking: pivot sqrt, column scaled by its reciprocal,
-// rank-1 update of the trailing lower triangle.  A non-positive pivot sets
+// shared memory, right-looking, one thread per entry (1024 threads): the pivot
+// d gives r = rsqrt(d), L_jj = d r, the column is scaled by r, then the
+// trailing lower triangle gets its rank-1 update.  GB300's FP64 latency makes
+// every dependent FP64 step costly, so each pivot takes one reciprocal square
+// root rather than a square root and a division.  A non-positive pivot sets
 // *info (first index) and stops; nothing runs once *info is set.
-// It also writes the leaf's own inverse L^-1 (lower, w x w) to inv[i + j*ldi]
-// for the solve of the rows below it.
-__global__ void __launch_bounds__(256) chol_leaf_kernel(double* A, long lda, int d0, int w, double* inv, int ldi,
-                                                       int32_t* info) {
-  __shared__ double D[kCholLeaf][kCholLeaf + 1];
+// It also writes the leaf's inverse L^-1 (lower, w x w) to inv[i + j*ldi],
+// formed by recursive doubling: the diagonal reciprocals, then for h = 1, 2,
+// 4, 8, 16 every pair of h x h diagonal blocks is joined,
+// X21 = -X22 (L21 X11), so the dependent chains are short dot products.
+__global__ void __launch_bounds__(1024) chol_leaf_kernel(double* A, long lda, int d0, int w, double* inv, int ldi,
+                                                        int32_t* info) {
+  __shared__ double D[kCholLeaf][kCholLeaf + 1], X[kCholLeaf][kCholLeaf + 1], T[kCholLeaf][kCholLeaf + 1];
+  __shared__ double rj;
   __shared__ int fail;
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, i = t & 31, j = t >> 5;
   if (t == 0) fail = (*info != 0);
   __syncthreads();
   if (fail) return;
   double* blk = A + d0 + static_cast<long>(d0) * lda;
-  for (int e = t; e < w * w; e += blockDim.x) {
-    const int i = e % w, j = e / w;
-    if (i >= j) D[i][j] = blk[i + static_cast<long>(j) * lda];
-  }
+  // padding beyond w is the identity, so the inverse below needs no special case
+  D[i][j] = (i < w && j < w) ? (i >= j ? blk[i + static_cast<long>(j) * lda] : 0.0) : (i == j ? 1.0 : 0.0);
   __syncthreads();
   int done = w;
-  for (int j = 0; j < w; ++j) {
+  for (int jj = 0; jj < w; ++jj) {
     if (t == 0) {
-      const double d = D[j][j];
+      const double d = D[jj][jj];
       if (!(d > 0.0)) {
-        atomicCAS(info, 0, d0 + j + 1);
+        atomicCAS(info, 0, d0 + jj + 1);
         fail = 1;
       } else {
-        D[j][j] = sqrt(d);
+        const double r = rsqrt(d);
+        D[jj][jj] = d * r;
+        rj = r;
       }
     }
     __syncthreads();
     if (fail) {
-      done = j;
+      done = jj;
       break;
     }
-    const double r = 1.0 / D[j][j];
-    if (t > j && t < w) D[t][j] *= r;
+    if (j == jj && i > jj && i < w) D[i][jj] *= rj;
     __syncthreads();
-    // D[i][k] -= D[i][j] D[k][j] for j < k <= i < w
-    const int m = w - 1 - j;   // trailing size
-    for (int e = t; e < m * m; e += blockDim.x) {
-      const int i = j + 1 + e % m, k = j + 1 + e / m;
-      if (k <= i) D[i][k] = fma(-D[i][j], D[k][j], D[i][k]);
-    }
+    if (i > jj && j > jj && j <= i && i < w) D[i][j] = fma(-D[i][jj], D[j][jj], D[i][j]);
     __syncthreads();
   }
   // write back the columns that were finished (all of them unless a pivot failed)
-  for (int e = t; e < w * w; e += blockDim.x) {
-    const int i = e % w, j = e / w;
-    if (i >= j && j < done) blk[i + static_cast<long>(j) * lda] = D[i][j];
-  }
+  if (i < w && j < done && i >= j) blk[i + static_cast<long>(j) * lda] = D[i][j];
   if (done < w) return;
-  // inverse: thread j solves L x = e_j by forward substitution (x_i for i < j are 0)
-  if (t < w) {
-    const int j = t;
-    double xs[kCholLeaf];
-#pragma unroll
-    for (int i = 0; i < kCholLeaf; ++i) {
-      if (i < j || i >= w) {
-        xs[i] = 0.0;
-        continue;
-      }
-      double acc = (i == j) ? 1.0 : 0.0;
-#pragma unroll
-      for (int k = 0; k < kCholLeaf; ++k)
-        if (k >= j && k < i) acc = fma(-D[i][k], xs[k], acc);
-      xs[i] = acc / D[i][i];
+  X[i][j] = (i == j) ? 1.0 / D[i][i] : 0.0;
+  __syncthreads();
+  for (int h = 1; h < kCholLeaf; h <<= 1) {
+    const int o = (i / (2 * h)) * (2 * h);
+    const bool in21 = (j / (2 * h) == i / (2 * h)) && (i - o >= h) && (j - o < h);
+    if (in21) {   // T21 = L21 X11
+      double acc = 0.0;
+      for (int k = j; k < o + h; ++k) acc = fma(D[i][k], X[k][j], acc);
+      T[i][j] = acc;
     }
-#pragma unroll
-    for (int i = 0; i < kCholLeaf; ++i)
-      if (i < w) inv[i + static_cast<long>(j) * ldi] = xs[i];
+    __syncthreads();
+    if (in21) {   // X21 = -X22 T21
+      double acc = 0.0;
+      for (int k = o + h; k <= i; ++k) acc = fma(X[i][k], T[k][j], acc);
+      X[i][j] = -acc;
+    }
+    __syncthreads();
   }
+  if (i < w && j < w) inv[i + static_cast<long>(j) * ldi] = X[i][j];
 }
 
 // C(i, j) = beta C(i, j) + alpha sum_l A(i, l) B(j, l) in FP64, for the m x n
@@ -658,6 +654,9 @@ __global__ void __launch_bounds__(256) trtri_cols_kernel(const double* A, long l
   const int i = threadIdx.x;
   const int j0 = blockIdx.x, j1 = nb - 1 - static_cast<int>(blockIdx.x);
   double x0 = (i == j0) ? 1.0 : 0.0, x1 = (i == j1) ? 1.0 : 0.0;
+  // every row's reciprocal at once: the steps below then multiply (a division
+  // on each step's dependent path would cost its full FP64 latency 256 times)
+  const double rinv = (!unit && i < nb) ? 1.0 / L[i + static_cast<long>(i) * lda] : 1.0;
   double ln[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) {
@@ -681,8 +680,8 @@ __global__ void __launch_bounds__(256) trtri_cols_kernel(const double* A, long l
       if (kk >= nb) break;
       if (i == kk) {
         if (!unit) {
-          x0 = x0 / lv[q];
-          x1 = x1 / lv[q];
+          x0 *= rinv;
+          x1 *= rinv;
         }
         bc[kk & 1][0] = x0;
         bc[kk & 1][1] = x1;
@@ -950,8 +949,8 @@ size_t lu_extra_bytes(int nb, int nsm) {
 int chol_diag(emul_handle_t h, double* A, long lda, int d0, int jb, double* inv, int32_t* info, bool want_inv) {
   for (int c0 = 0; c0 < jb; c0 += kCholLeaf) {
     const int wp = kCholLeaf < jb - c0 ? kCholLeaf : jb - c0;
-    chol_leaf_kernel<<<1, 256, 0, h->stream>>>(A, lda, d0 + c0, wp, inv + c0 + static_cast<long>(c0) * jb, jb,
-                                               info);
+    chol_leaf_kernel<<<1, 1024, 0, h->stream>>>(A, lda, d0 + c0, wp, inv + c0 + static_cast<long>(c0) * jb, jb,
+                                                info);
     h->launches++;
     const int r0 = c0 + wp, mr = jb - r0;
     if (mr > 0) {
@@ -1152,10 +1151,17 @@ __device__ bool solve_sync(unsigned long long* cnt, unsigned long long target, l
 // every block applies the block's column of L (or U) to 32-row groups of the
 // remaining rows.  Two bounded grid barriers per step.  A row's owner changes
 // from step to step, so x is read and written through L2 only.
-__device__ void solve_stage(const double* LU, long lda, int d0, int bs, bool lower, double* tb, double* rcp) {
+// Stage the bs x bs diagonal block at d0 for the block solve.  LU factors
+// (chol = false): the block as stored, rcp = 1/diag for the upper (backward)
+// solve.  Cholesky factor (chol = true): the forward solve uses L itself and
+// the backward solve L^T, so the block is staged transposed there; rcp = 1/diag
+// for both.
+__device__ void solve_stage(const double* LU, long lda, int d0, int bs, bool lower, double* tb, double* rcp,
+                            bool chol) {
   constexpr int ld = kSolveBs + 1;
   const int tid = threadIdx.x;
   const int r = tid & 127, cstep = blockDim.x >> 7;
+  const bool tr = chol && !lower;
   if (r < bs)
     for (int c0 = tid >> 7; c0 < bs; c0 += 16 * cstep) {
       double v[16];
@@ -1165,14 +1171,22 @@ __device__ void solve_stage(const double* LU, long lda, int d0, int bs, bool low
         v[j] = c < bs ? __ldg(LU + (d0 + r) + static_cast<long>(d0 + c) * lda) : 0.0;
       }
 #pragma unroll
-      for (int j = 0; j < 16; ++j)
-        if (c0 + j * cstep < bs) tb[r + (c0 + j * cstep) * ld] = v[j];
+      for (int j = 0; j < 16; ++j) {
+        const int c = c0 + j * cstep;
+        if (c < bs) tb[tr ? c + r * ld : r + c * ld] = v[j];
+      }
     }
   __syncthreads();
-  if (!lower && tid < bs) rcp[tid] = 1.0 / tb[tid + tid * ld];
+  if ((chol || !lower) && tid < bs) rcp[tid] = 1.0 / tb[tid + tid * ld];
   __syncthreads();
 }
 
+// CHOL = false: A = L U from the LU (unit L below the diagonal, U on and
+// above it).  CHOL = true: A = L L^T from the lower Cholesky factor, forward
+// with L (non-unit diagonal) and backward with L^T, whose rows are columns of
+// L: the update of the rows above a block then reads each column of L
+// contiguously, one warp per row of L^T.
+template <bool CHOL>
 __global__ void __launch_bounds__(256) getrs1_kernel(const double* LU, long lda, int n, double* x,
                                                      unsigned long long* cnt, int* status, long long limit) {
   extern __shared__ double tb[];   // kSolveBs x (kSolveBs + 1) staging of a diagonal block
@@ -1196,7 +1210,7 @@ __global__ void __launch_bounds__(256) getrs1_kernel(const double* LU, long lda,
     info(st, lower, d0, bs);
     const int sb = st % G, nxt = (st + 1) % G;
     if (b == sb) {
-      if (staged != st) solve_stage(LU, lda, d0, bs, lower, tb, rcp);
+      if (staged != st) solve_stage(LU, lda, d0, bs, lower, tb, rcp, CHOL);
       staged = -1;
       if (tid < 32) {
         double v[4];
@@ -1208,6 +1222,7 @@ __global__ void __launch_bounds__(256) getrs1_kernel(const double* LU, long lda,
             for (int kk = 0; kk < 32; ++kk) {
               const int k = 32 * q0 + kk;
               if (k >= bs) break;
+              if (CHOL && lane == kk) v[q0] = v[q0] * rcp[k];
               const double xk = __shfl_sync(0xFFFFFFFFu, v[q0], kk);
 #pragma unroll
               for (int q = q0; q < 4; ++q) {
@@ -1239,14 +1254,27 @@ __global__ void __launch_bounds__(256) getrs1_kernel(const double* LU, long lda,
       bool l2;
       int e0, es;
       info(st + 1, l2, e0, es);
-      solve_stage(LU, lda, e0, es, l2, tb, rcp);
+      solve_stage(LU, lda, e0, es, l2, tb, rcp, CHOL);
       staged = st + 1;
     }
     target += G;
     if (!solve_sync(cnt, target, limit, status)) return;
     // rows below (forward) or above (backward) the block, 32-row groups over all warps
     const int r_lo = lower ? d0 + bs : 0, r_hi = lower ? n : d0;
-    if (r_hi > r_lo) {
+    if (CHOL && !lower && r_hi > r_lo) {
+      // x_r -= sum_c L(d0 + c, r) x_c: one warp per row r, lanes along the column
+      for (int c = tid; c < bs; c += blockDim.x) xs[c] = __ldcg(x + d0 + c);
+      __syncthreads();
+      const int wpb = blockDim.x >> 5;
+      for (int r = r_lo + b * wpb + warp; r < r_hi; r += G * wpb) {
+        const double* col = LU + d0 + static_cast<long>(r) * lda;
+        double acc = 0.0;
+        for (int c = lane; c < bs; c += 32) acc = fma(__ldg(col + c), xs[c], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+        if (lane == 0) __stcg(x + r, __ldcg(x + r) - acc);
+      }
+    } else if (r_hi > r_lo) {
       for (int c = tid; c < bs; c += blockDim.x) xs[c] = __ldcg(x + d0 + c);
       __syncthreads();
       const int wpb = blockDim.x >> 5;
@@ -1277,7 +1305,7 @@ int getrs_body(emul_handle_t h, int n, int nrhs, const double* LU, int lda, cons
     unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ws);
     double* tmp = reinterpret_cast<double*>(ws + kAl);
     smem_attr(reinterpret_cast<const void*>(permute_rhs_kernel), kPermSmemMax * 4);
-    smem_attr(reinterpret_cast<const void*>(getrs1_kernel), kSolveBs * (kSolveBs + 1) * 8);
+    smem_attr(reinterpret_cast<const void*>(getrs1_kernel<false>), kSolveBs * (kSolveBs + 1) * 8);
     permute_rhs_kernel<<<1, 1024, static_cast<size_t>(n) * 4, h->stream>>>(ipiv, n, B, tmp);
     h->launches++;
     rc = check_cuda(h, cudaGetLastError(), "rhs permutation");
@@ -1290,7 +1318,7 @@ int getrs_body(emul_handle_t h, int n, int nrhs, const double* LU, int lda, cons
     void* args[] = {const_cast<double**>(&LU), &ldl, &n, &B, &cnt, &status, &limit};
     h->launches++;
     return check_cuda(h,
-                      cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(getrs1_kernel), dim3(h->nsm),
+                      cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(getrs1_kernel<false>), dim3(h->nsm),
                                                   dim3(256), args, kSolveBs * (kSolveBs + 1) * 8, h->stream),
                       "solve");
   }
@@ -1547,6 +1575,28 @@ int emul_dpotrs(emul_handle_t h, char uplo, int n, int nrhs, const double* L, in
     return emul::set_error(h, EMUL_INVALID_ARG, "emul_dpotrs: invalid argument");
   if (n == 0 || nrhs == 0) return EMUL_OK;
   const int ph = emul::phase_begin(h, EMUL_PHASE_SOLVE);
+  if (nrhs == 1) {
+    // one right-hand side: both substitutions in one cooperative launch
+    int rc = emul::reserve_workspace(h, emul::kAl);
+    if (rc) return rc;
+    unsigned long long* cnt = static_cast<unsigned long long*>(h->ws);
+    rc = emul::check_cuda(h, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), h->stream), "solve barrier");
+    if (rc) return rc;
+    emul::smem_attr(reinterpret_cast<const void*>(emul::getrs1_kernel<true>),
+                    emul::kSolveBs * (emul::kSolveBs + 1) * 8);
+    long ldl = lda;
+    long long limit = h->wait_limit;
+    int* status = h->d_status;
+    void* args[] = {const_cast<double**>(&L), &ldl, &n, &B, &cnt, &status, &limit};
+    h->launches++;
+    rc = emul::check_cuda(h,
+                          cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(emul::getrs1_kernel<true>),
+                                                      dim3(h->nsm), dim3(256), args,
+                                                      emul::kSolveBs * (emul::kSolveBs + 1) * 8, h->stream),
+                          "Cholesky solve");
+    emul::phase_end(h, ph);
+    return rc;
+  }
   constexpr int bs = 128;
   for (int d0 = 0; d0 < n; d0 += bs) {
     const int b = bs < n - d0 ? bs : n - d0;

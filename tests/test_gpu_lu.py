@@ -168,6 +168,20 @@ def test_potrf_potrs(gpu_lib, n, nb, cond, s):
     assert residual.backward_error(A, x, b) < 16
 
 
+def test_potrs_multiple_rhs(gpu_lib):
+    n, nrhs = 300, 4
+    A = inputs.spd(n, 1e6, seed=75)
+    B = inputs.uniform(n, nrhs, seed=76)
+    dA = ColMajor.from_numpy(A)
+    info = gpu_lib.dpotrf(dA, nb=64, slices=8)
+    assert int(info.item()) == 0
+    dB = ColMajor.from_numpy(B, ld=n + 5)
+    gpu_lib.dpotrs(dA, dB)
+    X = dB.numpy()
+    for j in range(nrhs):
+        assert residual.backward_error(A, X[:, j], B[:, j]) < 16
+
+
 @pytest.mark.parametrize("nb,at", [(32, 150), (256, 300), (256, 45)])
 def test_potrf_not_spd(gpu_lib, nb, at):
     """A negative diagonal entry makes the leading minor of that order
