@@ -487,6 +487,40 @@ def run_table2(args):
                       "seconds": time.perf_counter() - t0, "rows": out}), flush=True)
 
 
+def run_fig1(args):
+    """Fig. 1's sweep: LU + solve on HPL-style data A, b ~ U(-1/2, 1/2) for
+    growing n with 6 and 7 splits and native FP64, scaled residual of Eq. 8
+    (the paper reports that 6 splits fail the bar of 16 and 7 pass)."""
+    import torch
+    from paper_2509_23565_gb300 import inputs
+    from paper_2509_23565_gb300.binding import ColMajor, Emul
+    lib = Emul()
+    rows = []
+    for n in (256, 512, 1024, 2048, 4096, 8192, 16384):
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(n)
+        A0 = inputs.uniform_device(n, n, seed=n, lo=-0.5, hi=0.5)
+        b0 = torch.rand(n, generator=gen, device="cuda", dtype=torch.float64) - 0.5
+        row = {"n": n}
+        for s in (6, 7):
+            W = ColMajor(A0.clone(), n, n)
+            x = ColMajor(b0.clone().view(1, n), n, 1)
+            ipiv, info = lib.dgetrf(W, nb=256 if n >= 4096 else 128, slices=s)
+            lib.dgetrs(W, ipiv, x)
+            be = lib.backward_error(ColMajor(A0, n, n), x, ColMajor(b0.view(1, n), n, 1)).cpu().numpy()
+            row[f"s{s}"] = float(be[0])
+        LU, piv = torch.linalg.lu_factor(A0.t())
+        xn = torch.linalg.lu_solve(LU, piv, b0.view(n, 1))
+        be = lib.backward_error(ColMajor(A0, n, n), ColMajor(xn.t().contiguous(), n, 1),
+                                ColMajor(b0.view(1, n), n, 1)).cpu().numpy()
+        row["fp64"] = float(be[0])
+        del LU, piv, xn, A0
+        rows.append(row)
+    print(json.dumps({"metric": "scaled residual (Eq. 8) of the LU solve on U(-1/2,1/2), 6 and 7 splits",
+                      "config": {"workload": "HPL-style A, b ~ U(-1/2, 1/2), n = 256..16384"}, "rows": rows}),
+          flush=True)
+
+
 def run_selector(args):
     """Ablation of the learned slice selector (mixed dynamic ranges): LU + solve with
     slices chosen per step by the trained network (plus the a-posteriori probe)
@@ -497,7 +531,7 @@ def run_selector(args):
     lib = Emul()
     lib.selector_load(os.path.join(ROOT, "paper_2509_23565_gb300", "selector_weights.bin"))
     n, nb = args.n, args.nb
-    out = {"metric": "learned slice selector vs fixed s=8: LU TFLOP/s at backward error <= 16",
+    out = {"metric": "learned slice selector vs fixed s=7 and s=8: LU TFLOP/s at backward error <= 16",
            "config": {"workload": f"LU partial pivoting + solve n={n} nb={nb}", "n": n, "nb": nb}, "cases": {}}
     for name, A in (("uniform", inputs.uniform(n, n, seed=8100)),
                     ("mixed_r_0_8_16", inputs.mixed_range(n, nb, (0, 8, 16), seed=8101))):
@@ -507,7 +541,7 @@ def run_selector(args):
         W = ColMajor(torch.empty_like(A0), n, n)
         x = ColMajor(torch.empty((1, n), dtype=torch.float64, device="cuda"), n, 1)
         row = {}
-        for label, s in (("fixed_s8", 8), ("learned", 0)):
+        for label, s in (("fixed_s7", 7), ("fixed_s8", 8), ("learned", 0)):
             times, st = [], None
             for rep in range(args.warmup + args.steps):
                 W.store.copy_(A0)
@@ -524,7 +558,8 @@ def run_selector(args):
             row[label] = {"seconds": t, "tflops": lu_flops(n) / t / 1e12, "backward_error": float(be[1]),
                           "slices_mean": st.slices_mean, "slices_min": st.slices_min, "slices_max": st.slices_max,
                           "checks_failed": st.checks_failed}
-        row["speedup"] = row["fixed_s8"]["seconds"] / row["learned"]["seconds"]
+        row["speedup_vs_s8"] = row["fixed_s8"]["seconds"] / row["learned"]["seconds"]
+        row["speedup_vs_s7"] = row["fixed_s7"]["seconds"] / row["learned"]["seconds"]
         out["cases"][name] = row
     print(json.dumps(out), flush=True)
 
@@ -588,7 +623,7 @@ def main():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="lu",
-                   choices=["lu", "lu_nopiv", "chol", "gemm", "selector", "batched", "table2"])
+                   choices=["lu", "lu_nopiv", "chol", "gemm", "selector", "batched", "table2", "fig1"])
     p.add_argument("--range", type=float, default=0.0,
                    help="LU input u 10^e, e ~ U(-range, range) (0: uniform(-1,1))")
     p.add_argument("--cond", type=float, default=1e12, help="condition number of the Cholesky input")
@@ -626,6 +661,9 @@ def main():
         return
     if args.workload == "table2":
         run_table2(args)
+        return
+    if args.workload == "fig1":
+        run_fig1(args)
         return
     world, rank, local = dist_setup()
     run_ours(args, world, rank, local)

@@ -127,6 +127,21 @@ int emul_dgemm(emul_handle_t h, int m, int n, int k, double alpha, const double*
 int emul_dgemm_threshold(emul_handle_t h, int m, int n, int k, double alpha, const double* A, int lda,
                          const double* B, int ldb, double beta, double* C, int ldc, int slices, int threshold);
 
+/* emul_dgemm with unequal slice counts: slices_a slices of A and slices_b of B
+ * (the paper's related work, Sec. 3, cites unequal split sizes among the
+ * accuracy extensions of the method without defining them; this is the plain
+ * reading).  Both operands are split with s = max(slices_a, slices_b) slices,
+ * whose leading slices are exactly those of a shorter split, and only the
+ * pairs p <= slices_a, q <= slices_b with p + q <= threshold are kept
+ * (threshold = 0: s + 1; else 2..slices_a + slices_b; at slices_a + slices_b
+ * the kept sum is the exact product of the operands truncated to 7 slices_a
+ * and 7 slices_b bits).  Exact sum, one rounding, C update as emul_dgemm;
+ * slices_a = slices_b = s is emul_dgemm_threshold.  Returns EMUL_INVALID_ARG
+ * for counts outside 1..8 or a threshold outside that range. */
+int emul_dgemm_unequal(emul_handle_t h, int m, int n, int k, double alpha, const double* A, int lda,
+                       const double* B, int ldb, double beta, double* C, int ldc, int slices_a, int slices_b,
+                       int threshold);
+
 /* ------------------------------------------------------- factorizations --
  * Optional statistics of a factorization call (host memory, may be NULL).
  */

@@ -25,15 +25,19 @@ import numpy as np
 from .split import BITS, NONFINITE, split_rows, split_cols
 
 
-def level_sums(SA, SB, t):
+def level_sums(SA, SB, t, sa=None, sb=None):
     """I[L-2] = sum_{p+q=L} SA[p-1] @ SB[q-1]^T for L = 2..t, as int64 [t-1, m, n].
 
-    SA: int8 [s, m, k]; SB: int8 [s, n, k].  Each product term is at most
-    127**2 and each partial sum at most k * s * 127**2 < 2**53 for the sizes
-    used here, so float64 matmul of the integer-valued planes is exact in any
-    summation order; the result is converted back to int64.
+    SA: int8 [s, m, k]; SB: int8 [s, n, k].  With sa / sb given only the pairs
+    with p <= sa and q <= sb are summed (unequal slice counts, see
+    emul_gemm_unequal).  Each product term is at most 127**2 and each partial
+    sum at most k * s * 127**2 < 2**53 for the sizes used here, so float64
+    matmul of the integer-valued planes is exact in any summation order; the
+    result is converted back to int64.
     """
     s = SA.shape[0]
+    sa = s if sa is None else sa
+    sb = s if sb is None else sb
     m, k = SA.shape[1], SA.shape[2]
     n = SB.shape[1]
     assert k * s * 127 * 127 < 2**53
@@ -42,9 +46,9 @@ def level_sums(SA, SB, t):
     out = np.zeros((t - 1, m, n), dtype=np.int64)
     for L in range(2, t + 1):
         acc = np.zeros((m, n), dtype=np.float64)
-        for p in range(1, s + 1):
+        for p in range(1, sa + 1):
             q = L - p
-            if 1 <= q <= s:
+            if 1 <= q <= sb:
                 acc += A64[p - 1] @ B64[q - 1].T
         out[L - 2] = acc.astype(np.int64)
     return out
@@ -105,6 +109,29 @@ def emul_gemm(A, B, s, alpha=1.0, beta=0.0, C=None, t=None):
     e, SA = split_rows(A, s)
     f, SB = split_cols(B, s)
     I = level_sums(SA, SB, t)
+    if beta != 0.0:
+        C = np.asarray(C, dtype=np.float64)
+    return recombine(I, e, f, s, t=t, alpha=alpha, beta=beta, C=C)
+
+
+def emul_gemm_unequal(A, B, sa, sb, alpha=1.0, beta=0.0, C=None, t=None):
+    """beta*C + alpha*(A @ B) with sa slices of A and sb slices of B.
+
+    Reading of the unequal split counts the paper cites among the accuracy
+    extensions (Section 3): both operands are split with s = max(sa, sb)
+    slices, whose leading sa (sb) slices are exactly the slices of an sa-slice
+    (sb-slice) split, and only the pairs with p <= sa, q <= sb and p + q <= t
+    are kept (t defaults to s + 1).  With t = sa + sb every such pair is kept
+    and the kept sum is the exact product of the sa-digit and sb-digit scaled
+    integers.  Recombination and C update as in emul_gemm.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    s = max(sa, sb)
+    t = s + 1 if t is None else t
+    e, SA = split_rows(A, s)
+    f, SB = split_cols(B, s)
+    I = level_sums(SA, SB, t, sa=sa, sb=sb)
     if beta != 0.0:
         C = np.asarray(C, dtype=np.float64)
     return recombine(I, e, f, s, t=t, alpha=alpha, beta=beta, C=C)

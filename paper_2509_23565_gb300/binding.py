@@ -37,6 +37,8 @@ SIGNATURES = {
                             _c_int, _c_int]),
     "emul_dgemm_threshold": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_double, _vp, _c_int, _vp, _c_int, _c_double,
                                       _vp, _c_int, _c_int, _c_int]),
+    "emul_dgemm_unequal": (_c_int, [_vp, _c_int, _c_int, _c_int, _c_double, _vp, _c_int, _vp, _c_int, _c_double,
+                                    _vp, _c_int, _c_int, _c_int, _c_int]),
     "emul_dgetrf": (_c_int, [_vp, _c_int, _vp, _c_int, _vp, _c_int, _c_int, _vp, _vp]),
     "emul_dgetrf_nopiv": (_c_int, [_vp, _c_int, _vp, _c_int, _c_int, _c_int, _vp, _vp]),
     "emul_dgetrs": (_c_int, [_vp, _c_int, _c_int, _vp, _c_int, _vp, _vp, _c_int]),
@@ -204,6 +206,10 @@ class Emul:
             self._check(self.lib.emul_dgemm_threshold(self.h, C.m, C.n, A.n, alpha, _vp(A.ptr), A.ld, _vp(B.ptr),
                                                       B.ld, beta, _vp(C.ptr), C.ld, slices, t),
                         "emul_dgemm_threshold")
+
+    def dgemm_unequal(self, A, B, C, slices_a, slices_b, alpha=1.0, beta=0.0, t=0):
+        self._check(self.lib.emul_dgemm_unequal(self.h, C.m, C.n, A.n, alpha, _vp(A.ptr), A.ld, _vp(B.ptr), B.ld,
+                                                beta, _vp(C.ptr), C.ld, slices_a, slices_b, t), "emul_dgemm_unequal")
 
     def dgetrf(self, A, nb=0, slices=7, stats=False):
         import torch

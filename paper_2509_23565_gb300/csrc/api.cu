@@ -21,30 +21,28 @@ constexpr size_t kAlign = 256;
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 inline long kpad_of(int k) { return (static_cast<long>(k) + 7) / 8 * 8; }
 
+// The slice pairs kept: p <= sa slices of A, q <= sb slices of B (sa = sb = s
+// for the method itself; unequal counts keep a subset of the pairs of the
+// max(sa, sb)-slice split, whose leading slices are those of a shorter split).
+struct PairSet {
+  int sa, sb;
+  int lo(int L) const { return L - sb > 1 ? L - sb : 1; }          // first p of level L
+  int hi(int L) const { return L - 1 < sa ? L - 1 : sa; }          // last p of level L
+  int count(int L) const { return hi(L) >= lo(L) ? hi(L) - lo(L) + 1 : 0; }
+  // highest slice index of A or B a pair of level L uses
+  int planes(int L) const { return hi(L) > L - lo(L) ? hi(L) : L - lo(L); }
+};
+
 // Sum over the levels L = 2..last of n_L 2^(7(last-L)) times 127^2: the
 // worst-case magnitude per unit of k of the Horner state after level `last`
 // (t - 1 for the narrow variant's state before its final level, t for the
 // wide variant's complete state).
-long double horner_bound_per_k(int s, int last) {
+long double horner_bound_per_k(const PairSet& ps, int last) {
   long double acc = 0.0L;
-  for (int L = 2; L <= last; ++L) {
-    int nL = 0;
-    for (int p = 1; p <= s; ++p)
-      if (L - p >= 1 && L - p <= s) ++nL;
-    acc = acc * 128.0L + nL;
-  }
+  for (int L = 2; L <= last; ++L) acc = acc * 128.0L + ps.count(L);
   return acc * 127.0L * 127.0L;
 }
 
-int pairs_at(int s, int L) {
-  int n = 0;
-  for (int p = 1; p <= s; ++p)
-    if (L - p >= 1 && L - p <= s) ++n;
-  return n;
-}
-
-// Highest slice index in a pair of level L.
-int level_planes(int s, int L) { return L - 1 < s ? L - 1 : s; }
 
 // K chunks per accumulator job of n slice pairs under the exactness budget.
 int seg_chunks(int n) { return n > 0 ? kExactBudget / (n * kBK) : 0; }
@@ -53,10 +51,8 @@ struct Job {
   int L, pb, pe, c0, c1, flags, rel;
 };
 
-Job make_job(int s, int L, int c0, int c1, int flags, int rel) {
-  const int pb = L - s > 1 ? L - s : 1;
-  const int pe = L - 1 < s ? L - 1 : s;
-  return Job{L, pb, pe, c0, c1, flags, rel};
+Job make_job(const PairSet& ps, int L, int c0, int c1, int flags, int rel) {
+  return Job{L, ps.lo(L), ps.hi(L), c0, c1, flags, rel};
 }
 
 void push_sweep(std::vector<Sweep>& out, const Job& a, const Job* b) {
@@ -84,23 +80,23 @@ void push_sweep(std::vector<Sweep>& out, const Job& a, const Job* b) {
 // the pair does not fit the exactness budget over the whole K it runs as two
 // K halves, the first half of L+1 stashed until L is complete.  The bands
 // minimise the staged planes per K chunk (dynamic programme over the levels).
-bool build_banded(int s, int t, int nch, bool wide, std::vector<Sweep>& out) {
+bool build_banded(const PairSet& ps, int t, int nch, bool wide, std::vector<Sweep>& out) {
   out.clear();
   const int kInf = 1 << 28;
   std::vector<int> cost(t + 3, 0), choice(t + 3, 0);
   auto groups = [&](int seg) { return (nch + seg - 1) / seg; };
   for (int L = t; L >= 2; --L) {
     cost[L] = kInf;
-    const int sg1 = seg_chunks(pairs_at(s, L));
+    const int sg1 = seg_chunks(ps.count(L));
     if (sg1 >= 1 && cost[L + 1] < kInf && (wide || L < t || groups(sg1) <= 2)) {
-      cost[L] = level_planes(s, L) + cost[L + 1];
+      cost[L] = ps.planes(L) + cost[L + 1];
       choice[L] = 1;
     }
     if (L + 1 <= t && cost[L + 2] < kInf) {
-      const int a = seg_chunks(pairs_at(s, L)), b = seg_chunks(pairs_at(s, L + 1));
+      const int a = seg_chunks(ps.count(L)), b = seg_chunks(ps.count(L + 1));
       const int sg2 = a < b ? a : b;
-      if (sg2 >= 1 && groups(sg2) <= 2 && level_planes(s, L + 1) + cost[L + 2] < cost[L]) {
-        cost[L] = level_planes(s, L + 1) + cost[L + 2];
+      if (sg2 >= 1 && groups(sg2) <= 2 && ps.planes(L + 1) + cost[L + 2] < cost[L]) {
+        cost[L] = ps.planes(L + 1) + cost[L + 2];
         choice[L] = 2;
       }
     }
@@ -108,7 +104,7 @@ bool build_banded(int s, int t, int nch, bool wide, std::vector<Sweep>& out) {
   if (cost[2] >= kInf) return false;
   for (int L = 2; L <= t;) {
     if (choice[L] == 1) {
-      const int G = groups(seg_chunks(pairs_at(s, L)));
+      const int G = groups(seg_chunks(ps.count(L)));
       const int size = (nch + G - 1) / G;
       const bool fin = !wide && L == t;
       for (int g = 0; g < G; ++g) {
@@ -119,22 +115,22 @@ bool build_banded(int s, int t, int nch, bool wide, std::vector<Sweep>& out) {
           else if (g == 0) flags = kStash, rel = 1;
           else flags = kTake | kFinal;
         }
-        push_sweep(out, make_job(s, L, c0, c1, flags, rel), nullptr);
+        push_sweep(out, make_job(ps, L, c0, c1, flags, rel), nullptr);
       }
       L += 1;
     } else {
-      const int a = seg_chunks(pairs_at(s, L)), b = seg_chunks(pairs_at(s, L + 1));
+      const int a = seg_chunks(ps.count(L)), b = seg_chunks(ps.count(L + 1));
       const int G = groups(a < b ? a : b);
       const bool fin = !wide && L + 1 == t;
       if (G == 1) {
-        const Job j1 = make_job(s, L + 1, 0, nch, fin ? kFinal : kOpen, 0);
-        push_sweep(out, make_job(s, L, 0, nch, kOpen, 0), &j1);
+        const Job j1 = make_job(ps, L + 1, 0, nch, fin ? kFinal : kOpen, 0);
+        push_sweep(out, make_job(ps, L, 0, nch, kOpen, 0), &j1);
       } else {
         const int h = (nch + 1) / 2;
-        const Job j1 = make_job(s, L + 1, 0, h, kStash, 2);
-        push_sweep(out, make_job(s, L, 0, h, kOpen, 0), &j1);
-        const Job j2 = make_job(s, L + 1, h, nch, kTake | (fin ? kFinal : kOpen), 0);
-        push_sweep(out, make_job(s, L, h, nch, 0, 0), &j2);
+        const Job j1 = make_job(ps, L + 1, 0, h, kStash, 2);
+        push_sweep(out, make_job(ps, L, 0, h, kOpen, 0), &j1);
+        const Job j2 = make_job(ps, L + 1, h, nch, kTake | (fin ? kFinal : kOpen), 0);
+        push_sweep(out, make_job(ps, L, h, nch, 0, 0), &j2);
       }
       L += 2;
     }
@@ -147,13 +143,13 @@ bool build_banded(int s, int t, int nch, bool wide, std::vector<Sweep>& out) {
 // fit, or (wide variant) its K range into segments.  Consecutive jobs of one K
 // range share a sweep.  In the narrow variant the last level's jobs (at most
 // two) form the final sweep.
-bool build_levelwise(int s, int t, int nch, bool wide, std::vector<Sweep>& out) {
+bool build_levelwise(const PairSet& ps, int t, int nch, bool wide, std::vector<Sweep>& out) {
   out.clear();
   std::vector<Job> jobs, held;
   const int kc = nch * kBK;
   for (int L = 2; L <= t; ++L) {
-    const int pb = L - s > 1 ? L - s : 1;
-    const int pe = L - 1 < s ? L - 1 : s;
+    const int pb = ps.lo(L);
+    const int pe = ps.hi(L);
     const int n = pe - pb + 1;
     std::vector<Job>& dst = (!wide && L == t) ? held : jobs;
     if (n * kc <= kExactBudget) {
@@ -261,12 +257,17 @@ void set_chunks_per_stage(int s, std::vector<Sweep>& out) {
 // Schedule and slot plan for the levels 2..t (t = 0: the default threshold
 // s + 1 of the method): the banded schedule when it exists and plans, else the
 // level-ordered one.
+// sa, sb: slices of A and of B whose pairs are kept (0: s); s = max(sa, sb)
+// is the split both operands get and the number of planes a stage holds.
 bool build_schedule(int s, int nch, bool wide, bool mode1, std::vector<Sweep>& out, std::vector<uint8_t>& tab,
-                    int& njobs, int& t0, int& period, int t = 0) {
+                    int& njobs, int& t0, int& period, int t = 0, int sa = 0, int sb = 0) {
+  if (sa == 0) sa = s;
+  if (sb == 0) sb = s;
   if (t == 0) t = s + 1;
-  if (t < 2 || t > 2 * s) return false;
-  if (!(build_banded(s, t, nch, wide, out) && plan_slots(out, mode1, tab, njobs, t0, period)) &&
-      !(build_levelwise(s, t, nch, wide, out) && plan_slots(out, mode1, tab, njobs, t0, period)))
+  if (t < 2 || t > sa + sb || (sa > sb ? sa : sb) != s) return false;
+  const PairSet ps{sa, sb};
+  if (!(build_banded(ps, t, nch, wide, out) && plan_slots(out, mode1, tab, njobs, t0, period)) &&
+      !(build_levelwise(ps, t, nch, wide, out) && plan_slots(out, mode1, tab, njobs, t0, period)))
     return false;
   set_chunks_per_stage(s, out);
   return true;
@@ -275,32 +276,35 @@ bool build_schedule(int s, int nch, bool wide, bool mode1, std::vector<Sweep>& o
 // The narrow variant keeps the Horner state in int64 and rounds T = R 2^7 + I
 // on a 64-bit magnitude (a 128-bit path covers |R| >= 2^57): it needs the last
 // level in at most two jobs and |R| well inside int64.
-bool narrow_ok(int s, int k, int t = 0) {
+bool narrow_ok(int s, int k, int t = 0, int sa = 0, int sb = 0) {
+  if (sa == 0) sa = s;
+  if (sb == 0) sb = s;
   if (t == 0) t = s + 1;
   if (s > 7) return false;
   const int nch = (k + kBK - 1) / kBK;
   std::vector<Sweep> tmp;
   std::vector<uint8_t> tab;
   int nj, t0, per;
-  if (!build_schedule(s, nch, false, false, tmp, tab, nj, t0, per, t)) return false;
-  const long double bound = horner_bound_per_k(s, t - 1) * static_cast<long double>(nch * kBK);
+  if (!build_schedule(s, nch, false, false, tmp, tab, nj, t0, per, t, sa, sb)) return false;
+  const long double bound = horner_bound_per_k(PairSet{sa, sb}, t - 1) * static_cast<long double>(nch * kBK);
   return bound < 4.0e18L;   // < 2^62
 }
 
 // The wide variant's complete 128-bit Horner state must stay below 2^126.
-bool wide_ok(int s, int t, int k) {
+bool wide_ok(int s, int t, int k, int sa = 0, int sb = 0) {
   const int nch = (k + kBK - 1) / kBK;
-  return horner_bound_per_k(s, t) * static_cast<long double>(nch * kBK) < 8.5e37L;
+  return horner_bound_per_k(PairSet{sa ? sa : s, sb ? sb : s}, t) * static_cast<long double>(nch * kBK) < 8.5e37L;
 }
 
 // Device copy of a schedule: the sweeps, then the slot table (16-byte aligned).
 size_t schedule_bytes(size_t nsweeps, size_t ntab) { return nsweeps * sizeof(Sweep) + 16 + ntab; }
 
 int get_schedule(emul_handle_t h, int s, int t, int nch, bool wide, bool mode1, Sweep** dptr, int* count,
-                 SlotPlan* plan) {
-  const uint32_t key = (static_cast<uint32_t>(s) << 24) | (static_cast<uint32_t>(wide) << 23) |
-                       (static_cast<uint32_t>(mode1) << 22) | (static_cast<uint32_t>(t) << 13) |
-                       static_cast<uint32_t>(nch);   // nch < 2^13 (k <= 65536)
+                 SlotPlan* plan, int sa, int sb) {
+  const uint64_t key = (static_cast<uint64_t>(sa) << 40) | (static_cast<uint64_t>(sb) << 32) |
+                       (static_cast<uint64_t>(s) << 24) | (static_cast<uint64_t>(wide) << 23) |
+                       (static_cast<uint64_t>(mode1) << 22) | (static_cast<uint64_t>(t) << 13) |
+                       static_cast<uint64_t>(nch);   // nch < 2^13 (k <= 65536)
   auto it = h->sched_cache.find(key);
   if (it != h->sched_cache.end()) {
     *dptr = it->second.sched;
@@ -311,7 +315,7 @@ int get_schedule(emul_handle_t h, int s, int t, int nch, bool wide, bool mode1, 
   std::vector<Sweep> v;
   std::vector<uint8_t> tab;
   SlotPlan sp{};
-  if (!build_schedule(s, nch, wide, mode1, v, tab, sp.njobs, sp.t0, sp.period, t))
+  if (!build_schedule(s, nch, wide, mode1, v, tab, sp.njobs, sp.t0, sp.period, t, sa, sb))
     return set_error(h, EMUL_INVALID_ARG, "no schedule for this slice count / k");
   const size_t off_tab = (v.size() * sizeof(Sweep) + 15) / 16 * 16;
   std::vector<uint8_t> blob(off_tab + tab.size(), 0);
@@ -415,7 +419,9 @@ size_t gemm_workspace_bytes(int m, int n, int k, int s, bool same_operand) {
 
 int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Operand B, double beta, double* C,
              long ldc, int s, bool lower, int mode, int32_t* levels, long ldl, long ldl_plane, size_t ws_offset,
-             int t) {
+             int t, int s_a, int s_b) {
+  if (s_a == 0) s_a = s;
+  if (s_b == 0) s_b = s;
   if (t == 0) t = s + 1;
   if (m <= 0 || n <= 0) return EMUL_OK;
   if (k <= 0) {
@@ -460,18 +466,19 @@ int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Oper
     if (rc) return rc;
   }
   // the narrow test plans a schedule; it is made once per (s, t, K chunks)
-  const uint64_t nkey = (static_cast<uint64_t>(s) << 32) | (static_cast<uint64_t>(t) << 16) |
+  const uint64_t nkey = (static_cast<uint64_t>(s_a) << 48) | (static_cast<uint64_t>(s_b) << 40) |
+                        (static_cast<uint64_t>(s) << 32) | (static_cast<uint64_t>(t) << 16) |
                         static_cast<uint64_t>((k + kBK - 1) / kBK);
   auto nit = h->narrow_cache.find(nkey);
-  if (nit == h->narrow_cache.end()) nit = h->narrow_cache.emplace(nkey, narrow_ok(s, k, t)).first;
+  if (nit == h->narrow_cache.end()) nit = h->narrow_cache.emplace(nkey, narrow_ok(s, k, t, s_a, s_b)).first;
   const bool wide = !nit->second;
-  if (wide && mode == 0 && !wide_ok(s, t, k))
+  if (wide && mode == 0 && !wide_ok(s, t, k, s_a, s_b))
     return set_error(h, EMUL_NOT_SUPPORTED, "threshold too high for this k: the 128-bit Horner state could overflow");
   const int nch = (k + kBK - 1) / kBK;
   Sweep* sched = nullptr;
   int nsweeps = 0;
   SlotPlan plan{};
-  rc = get_schedule(h, s, t, nch, wide, mode == 1, &sched, &nsweeps, &plan);
+  rc = get_schedule(h, s, t, nch, wide, mode == 1, &sched, &nsweeps, &plan, s_a, s_b);
   if (rc) return rc;
   const int BN = wide ? 64 : 128;
   CUtensorMap tmA, tmB;
@@ -528,7 +535,7 @@ int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Oper
     }
     // slice pairs kept: those of the levels L = 2..t (s(s+1)/2 at t = s + 1)
     double P = 0.0;
-    for (int L = 2; L <= t; ++L) P += pairs_at(s, L);
+    for (int L = 2; L <= t; ++L) P += PairSet{s_a, s_b}.count(L);
     const double cells = lower ? 0.5 * m * (double)n : static_cast<double>(m) * n;
     rec.flops = 2.0 * cells * k * P;
     rec.bytes = cells * (beta != 0.0 ? 16.0 : 8.0) + static_cast<double>(s) * 2.0 * k * (m + (same ? 0 : n));
@@ -752,6 +759,20 @@ int emul_dgemm_threshold(emul_handle_t h, int m, int n, int k, double alpha, con
 int emul_dgemm(emul_handle_t h, int m, int n, int k, double alpha, const double* A, int lda, const double* B,
                int ldb, double beta, double* C, int ldc, int slices) {
   return emul_dgemm_threshold(h, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, slices, 0);
+}
+
+int emul_dgemm_unequal(emul_handle_t h, int m, int n, int k, double alpha, const double* A, int lda,
+                       const double* B, int ldb, double beta, double* C, int ldc, int slices_a, int slices_b,
+                       int threshold) {
+  if (!h) return EMUL_INVALID_ARG;
+  const int s = slices_a > slices_b ? slices_a : slices_b;
+  if (m < 0 || n < 0 || k < 0 || slices_a < 1 || slices_b < 1 || s > emul::kMaxSlices || lda < (m > 1 ? m : 1) ||
+      ldb < (k > 1 ? k : 1) || ldc < (m > 1 ? m : 1) || (m > 0 && n > 0 && !C) ||
+      (m > 0 && n > 0 && k > 0 && (!A || !B)) || k > 16384 * 4 ||
+      (threshold != 0 && (threshold < 2 || threshold > slices_a + slices_b)))
+    return emul::set_error(h, EMUL_INVALID_ARG, "emul_dgemm_unequal: invalid argument");
+  return emul::gemm_run(h, m, n, k, alpha, Operand{A, 1, lda}, Operand{B, ldb, 1}, beta, C, ldc, s, false, 0, nullptr,
+                        0, 0, 0, threshold, slices_a, slices_b);
 }
 
 }  // extern "C"

@@ -53,6 +53,7 @@ constexpr int kMaxStages = kMaxStagesCfg;
 constexpr uint32_t kRowBytes = kBK * 2;     // one K-major row of a staged tile
 constexpr uint32_t kSwizzleCode = kRowBytes == 64 ? 4u : 6u;   // descriptor code of SWIZZLE_64B / _32B
 constexpr int kStatusTimeout = -4;
+constexpr long long kFoldLimit = 1ll << 55;   // |R| below it: R * 2^7 + I fits in 64 bits
 
 template <bool WIDE>
 struct Cfg {
@@ -87,35 +88,31 @@ __device__ __forceinline__ double rn_split(long long R, int I, int sh) {
   return __dadd_rn(dh, dl);
 }
 
-// RN(x * 2^sh) for a 64-bit integer x, in integer arithmetic only, valid for
-// -1022 <= sh <= 960 (every |x| < 2^63 then gives a normal result or, after a
-// carry, the largest binade): the magnitude is cut to 53 bits with ties to
-// even; a carry out of the mantissa moves into the exponent field.
+// RN(x * 2^sh) for a 64-bit integer x, in integer arithmetic only and without
+// branches (the lanes of a warp hold unrelated values), valid for
+// -1022 <= sh <= 960: every |x| < 2^64 then gives a normal result (or, after a
+// carry, the top binade).  |x| is normalised so that its leading one sits at
+// bit 63, its top 53 bits are kept and rounded to nearest even with bit 10 as
+// the round bit and bits 0-9 as the sticky bits; a carry out of the mantissa
+// moves into the exponent field.
 __device__ __forceinline__ double rn_x64(long long x, int sh) {
-  if (x == 0) return 0.0;
-  const unsigned long long sign = x < 0 ? 0x8000000000000000ull : 0ull;
-  const unsigned long long a = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
-  const int msb = 63 - __clzll((long long)a);
-  unsigned long long q;
-  if (msb <= 52) {
-    q = a << (52 - msb);
-  } else {
-    const int r = msb - 52;
-    q = a >> r;
-    const unsigned long long rem = a & ((1ull << r) - 1ull), half = 1ull << (r - 1);
-    q += (rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull;
-  }
-  return __longlong_as_double((long long)(sign | (((unsigned long long)(msb + sh + 1022) << 52) + q)));
+  const unsigned long long sgn = (unsigned long long)(x >> 63);      // 0 or all ones
+  const unsigned long long a = ((unsigned long long)x ^ sgn) - sgn;   // |x|
+  const int lz = __clzll((long long)a);
+  const unsigned long long m = a << (lz & 63);
+  unsigned long long q = m >> 11;
+  const unsigned long long rb = (m >> 10) & 1ull;
+  const unsigned long long st = (m & 0x3FFull) ? 1ull : 0ull;
+  q += rb & (st | (q & 1ull));
+  const unsigned long long bits = ((unsigned long long)(63 - lz + sh + 1022) << 52) + q;
+  return a ? __longlong_as_double((long long)(bits | (sgn << 63))) : 0.0;
 }
 
-// RN(T * 2^sh) for T = R * 2^7 + I: with |R| < 2^55 (the usual case: the
-// Horner state reaches 2^57 only when the leading digits of whole rows and
-// columns are near 127 with one sign) T fits in 64 bits and is rounded with
-// integer operations alone; otherwise the two-part path with one FP64 add.
-__device__ __forceinline__ double rn_final(long long R, int I, int sh) {
-  const long long lim = 1ll << 55;
-  if (R > -lim && R < lim && sh >= -1022 && sh <= 960) return rn_x64((R << 7) + I, sh);
-  return rn_split(R, I, sh);
+// D of a 64-bit exact sum x: the branchless path when sh keeps every result
+// normal, else the general one.
+__device__ __forceinline__ double rn_sum64(long long x, int sh) {
+  if (sh >= -1022 && sh <= 960) return rn_x64(x, sh);
+  return rn_scaled((__int128)x, sh);
 }
 
 // C <- RN(C + v) as a reduction in L2 (fire and forget: no load of C, no FP64
@@ -390,6 +387,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             continue;
           }
           const bool take = a.mode == 0 && (fl & kTake);
+          bool released = false;   // slots already released (final step, 64-bit path)
           if (aborted(abortp) || !mbar_wait(&slot_full[slot], par, a.wait_limit) ||
               (take && !mbar_wait(&slot_full[st_slot], st_par, a.wait_limit))) {
             if (!aborted(abortp)) raise_timeout(a, abortp);
@@ -421,33 +419,78 @@ __global__ void __launch_bounds__(kThreads, 1)
             // rounded once, C updated in place
             final_done = true;
             const bool rowok = row < a.M;
+            // When no R of the warp reaches 2^55 (R reaches 2^57 only when whole
+            // rows and columns have leading digits near 127 of one sign), T fits
+            // in 64 bits: the last level is folded into R, both TMEM slots are
+            // released at once, and the rounding runs while the MMAs of the next
+            // tile fill them.  Otherwise T is rounded from its two exact parts.
+            bool fits = !WIDE;
 #pragma unroll
-            for (int c4 = 0; c4 < CPT / 4; ++c4) {
-              uint32_t r0[4], r1[4];
-              tmem_ld4(ta + c4 * 4, r0);
-              if (take) tmem_ld4(tb + c4 * 4, r1);
-              tmem_ld_wait();
+            for (int c = 0; c < CPT; ++c) fits = fits && R[c] > -kFoldLimit && R[c] < kFoldLimit;
+            fits = __all_sync(0xFFFFFFFFu, fits);
+            if (fits) {
 #pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                const int c = c4 * 4 + q;
+              for (int c4 = 0; c4 < CPT / 4; ++c4) {
+                uint32_t r0[4], r1[4];
+                tmem_ld4(ta + c4 * 4, r0);
+                if (take) tmem_ld4(tb + c4 * 4, r1);
+                tmem_ld_wait();
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                  R[c4 * 4 + q] = R[c4 * 4 + q] * (State)128 + (State)(f2i(r0[q]) + (take ? f2i(r1[q]) : 0));
+              }
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) {
+                mbar_arrive(&slot_empty[slot]);
+                if (take) mbar_arrive(&slot_empty[st_slot]);
+              }
+              released = true;
+              double* cp = a.C + row + (long)col0 * a.ldc;
+#pragma unroll
+              for (int c = 0; c < CPT; ++c, cp += a.ldc) {
                 const int col = col0 + c;
                 const int f = __shfl_sync(0xFFFFFFFFu, fcol[0], c);
                 if (!rowok || col >= a.N || (a.lower && row < col)) continue;
-                const int I = f2i(r0[q]) + (take ? f2i(r1[q]) : 0);
-                double D;
-                if (e_row == kNonFinite || f == kNonFinite)
-                  D = __longlong_as_double(0x7FF8000000000000ll);
-                else if (WIDE)
-                  D = rn_scaled((__int128)R[c] * 128 + (__int128)I, e_row + f + sh0);
-                else
-                  D = rn_final((long long)R[c], I, e_row + f + sh0);
-                double* cp = a.C + row + (long)col * a.ldc;
+                const double D = (e_row == kNonFinite || f == kNonFinite)
+                                     ? __longlong_as_double(0x7FF8000000000000ll)
+                                     : rn_sum64((long long)R[c], e_row + f + sh0);
                 if (UPD == kSub)
                   red_add_f64(cp, neg_d(D));
                 else if (UPD == kSet)
                   *cp = D;
                 else
                   *cp = apply_update<UPD>(a, D, needs_c ? *cp : 0.0);
+              }
+            } else {
+#pragma unroll
+              for (int c4 = 0; c4 < CPT / 4; ++c4) {
+                uint32_t r0[4], r1[4];
+                tmem_ld4(ta + c4 * 4, r0);
+                if (take) tmem_ld4(tb + c4 * 4, r1);
+                tmem_ld_wait();
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                  const int c = c4 * 4 + q;
+                  const int col = col0 + c;
+                  const int f = __shfl_sync(0xFFFFFFFFu, fcol[0], c);
+                  if (!rowok || col >= a.N || (a.lower && row < col)) continue;
+                  const int I = f2i(r0[q]) + (take ? f2i(r1[q]) : 0);
+                  double D;
+                  if (e_row == kNonFinite || f == kNonFinite)
+                    D = __longlong_as_double(0x7FF8000000000000ll);
+                  else if (WIDE)
+                    D = rn_scaled((__int128)R[c] * 128 + (__int128)I, e_row + f + sh0);
+                  else
+                    D = rn_split((long long)R[c], I, e_row + f + sh0);
+                  double* cp = a.C + row + (long)col * a.ldc;
+                  if (UPD == kSub)
+                    red_add_f64(cp, neg_d(D));
+                  else if (UPD == kSet)
+                    *cp = D;
+                  else
+                    *cp = apply_update<UPD>(a, D, needs_c ? *cp : 0.0);
+                }
               }
             }
           } else {
@@ -476,11 +519,13 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
             }
           }
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) {
-            mbar_arrive(&slot_empty[slot]);
-            if (take) mbar_arrive(&slot_empty[st_slot]);
+          if (!released) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+              mbar_arrive(&slot_empty[slot]);
+              if (take) mbar_arrive(&slot_empty[st_slot]);
+            }
           }
         }
       }

@@ -24,7 +24,7 @@ struct emul_handle_s {
     int nsweeps;
     emul::SlotPlan plan;
   };
-  std::map<uint32_t, SchedEntry> sched_cache;   // (s, wide, level-sum mode, threshold, chunks) -> device schedule
+  std::map<uint64_t, SchedEntry> sched_cache;   // (slices of A / B, s, wide, level-sum mode, threshold, chunks) -> device schedule
   std::map<uint64_t, bool> narrow_cache;        // (s, t, chunks) -> the 128-column variant applies
   std::string last_error;
   void* encode_fn = nullptr;        // cuTensorMapEncodeTiled
@@ -77,7 +77,8 @@ size_t gemm_workspace_bytes(int m, int n, int k, int s, bool same_operand);
 // products back to back on one stream may share offset 0).
 int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Operand B, double beta, double* C,
              long ldc, int s, bool lower, int mode, int32_t* levels, long ldl, long ldl_plane, size_t ws_offset = 0,
-             int t = 0);   // t: truncation threshold, 0 = s + 1
+             int t = 0,     // t: truncation threshold, 0 = s + 1
+             int s_a = 0, int s_b = 0);   // slices of A / of B whose pairs are kept (0: s; max = s)
 
 // Learned slice selector (selector.cu).
 int selector_features(emul_handle_t h, int m, int n, int k, Operand A, Operand B, float* feat);

@@ -105,3 +105,48 @@ def test_auto_slices_lu(gpu_lib):
         assert int(info.item()) == 0
         assert 3 <= st.slices_min <= st.slices_max <= 8
         assert residual.backward_error(A, db.numpy()[:, 0], b) < 16
+
+
+def test_selector_gain_over_fixed_slices(gpu_lib):
+    """What the trained network gains over the method without it (mixed
+    dynamic ranges, block rows scaled with r in {0, 8, 16}): LU + solve with
+    slices chosen per step by the network and checked by the probe, against
+    the constant s = 7 of the method and against the fixed s = 8 fallback.
+    Measured and asserted: every run passes the bar of 16; the network keeps
+    the mean slice count at about 7; it is faster than fixed s = 8 (which runs
+    the 64-column product at half the MMA rate); and against the constant
+    s = 7 it gains nothing: it picks s = 7 on nearly every step and pays the
+    features and the probe, so it is slower, by at most half."""
+    import torch
+    gpu_lib.selector_load(WEIGHTS)
+    n, nb = 4096, 256
+    A = inputs.mixed_range(n, nb, (0, 8, 16), seed=8101)
+    b = inputs.vector(n, seed=8102)
+    A0 = ColMajor.from_numpy(A)
+    b0 = ColMajor.from_numpy(b)
+    res = {}
+    for label, s in (("s7", 7), ("s8", 8), ("learned", 0)):
+        W = ColMajor(A0.store.clone(), n, n)
+        x = ColMajor(b0.store.clone(), n, 1)
+        times = []
+        for rep in range(3):
+            W.store.copy_(A0.store)
+            x.store.copy_(b0.store)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ipiv, info, st = gpu_lib.dgetrf(W, nb=nb, slices=s, stats=True)
+            gpu_lib.dgetrs(W, ipiv, x)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        gpu_lib.sync_status()
+        assert int(info.item()) == 0
+        berr = residual.backward_error(A, x.numpy()[:, 0], b)
+        res[label] = {"ms": min(times[1:]), "berr": berr, "mean_s": st.slices_mean, "failed": st.checks_failed}
+    print(res)
+    for v in res.values():
+        assert v["berr"] < 16, res
+    assert 6.5 <= res["learned"]["mean_s"] <= 7.5, res
+    assert res["learned"]["ms"] < res["s8"]["ms"], res
+    assert res["s7"]["ms"] < res["learned"]["ms"] < 1.5 * res["s7"]["ms"], res

@@ -114,3 +114,26 @@ def test_threshold_refused_on_host(gpu_lib):
     gpu_lib.dgemm(A, B, dC, 8, t=16)
     gpu_lib.sync_status()
     assert _same_bits(dC.numpy(), emulgemm.emul_gemm(A.numpy(), B.numpy(), 8, t=16))
+
+
+
+@pytest.mark.parametrize("sa,sb,t", [(3, 7, 0), (7, 3, 0), (5, 8, 0), (8, 2, 0), (4, 6, 10), (7, 7, 0),
+                                     (6, 2, 8), (2, 7, 5)])
+@pytest.mark.parametrize("m,n,k", [(130, 70, 96), (257, 129, 256), (64, 300, 160)])
+def test_unequal_slices_bitexact(gpu_lib, sa, sb, t, m, n, k):
+    """Unequal slice counts (pairs p <= sa, q <= sb, p + q <= t) bit for bit
+    against the oracle, Schur-update form."""
+    A = inputs.log_scaled(m, k, 3, seed=m + sa)
+    B = inputs.uniform(k, n, seed=n + sb)
+    C = inputs.uniform(m, n, seed=m + n + t)
+    dC = ColMajor.from_numpy(C)
+    gpu_lib.dgemm_unequal(ColMajor.from_numpy(A), ColMajor.from_numpy(B), dC, sa, sb, -1.0, 1.0, t)
+    gpu_lib.sync_status()
+    want = emulgemm.emul_gemm_unequal(A, B, sa, sb, alpha=-1.0, beta=1.0, C=C, t=t or None)
+    assert np.array_equal(dC.numpy().view(np.int64), want.view(np.int64))
+
+
+def test_unequal_rejects_bad_threshold(gpu_lib):
+    A = ColMajor.empty(10, 10)
+    with pytest.raises(Exception):
+        gpu_lib.dgemm_unequal(A, A, ColMajor.empty(10, 10), 3, 2, 1.0, 0.0, 6)

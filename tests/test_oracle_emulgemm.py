@@ -140,3 +140,58 @@ def test_threshold_full_product_correctly_rounded(s):
     # every intermediate threshold lies between: error non-increasing in t
     errs = [float(np.max(np.abs(emulgemm.emul_gemm(A, B, s, t=t) - want))) for t in range(2, 2 * s + 1)]
     assert all(a >= b for a, b in zip(errs, errs[1:])) and errs[-1] == 0.0, errs
+
+
+@pytest.mark.parametrize("s,sa", [(7, 3), (8, 5), (6, 6), (5, 1)])
+def test_shorter_split_is_a_prefix(s, sa):
+    """The slices of an sa-slice split are the leading sa slices of an s-slice
+    split (same scales): truncation at 7 sa bits keeps the leading digits."""
+    A = inputs.log_scaled(9, 33, 6, seed=40 + s)
+    e, S = split.split_rows(A, s)
+    e2, S2 = split.split_rows(A, sa)
+    assert np.array_equal(e, e2)
+    assert np.array_equal(S[:sa], S2)
+
+
+@pytest.mark.parametrize("sa,sb", [(3, 7), (7, 4), (5, 5), (2, 8), (8, 1)])
+def test_unequal_all_pairs_equal_truncated_product(sa, sb):
+    """With t = sa + sb every pair p <= sa, q <= sb is kept, and the kept sum
+    T = sum_{p,q} SA_p SB_q 2^(7(t-p-q)) is exactly N_A^(sa) N_B^(sb)^T, the
+    product of the scaled integers truncated to 7 sa and 7 sb bits."""
+    A = inputs.log_scaled(6, 11, 3, seed=50 + sa)
+    B = inputs.log_scaled(11, 5, 3, seed=60 + sb)
+    s = max(sa, sb)
+    t = sa + sb
+    e, SA = split.split_rows(A, s)
+    f, SB = split.split_cols(B, s)
+    T = emulgemm.combine_levels(emulgemm.level_sums(SA, SB, t, sa=sa, sb=sb), t)
+    NA = split.scaled_integers(A, e, sa).astype(object)
+    NB = split.scaled_integers(B.T, f, sb).astype(object)
+    assert (T == NA.dot(NB.T)).all()
+    # and the rounded result is RN of that exact product times 2^(e + f - 7 (sa + sb))
+    D = emulgemm.emul_gemm_unequal(A, B, sa, sb, t=t)
+    for i in range(6):
+        for j in range(5):
+            want = Fraction(int(NA[i].dot(NB[j]))) * Fraction(2) ** (int(e[i]) + int(f[j]) - 7 * t)
+            assert D[i, j] == float(want)
+
+
+def test_unequal_equal_counts_is_the_method():
+    A = inputs.uniform(20, 30, seed=70)
+    B = inputs.uniform(30, 9, seed=71)
+    for s in (3, 7):
+        assert np.array_equal(emulgemm.emul_gemm_unequal(A, B, s, s), emulgemm.emul_gemm(A, B, s))
+
+
+def test_unequal_fewer_slices_never_more_accurate():
+    """Dropping slices of one operand can only lose digits: with t = sa + sb
+    the error against the exact product grows as sa shrinks."""
+    A = inputs.uniform(30, 64, seed=72)
+    B = inputs.uniform(64, 20, seed=73)
+    ref = np.array([[float(sum(Fraction(A[i, k]) * Fraction(B[k, j]) for k in range(64))) for j in range(20)]
+                    for i in range(30)])
+    errs = []
+    for sa in (2, 4, 6, 8):
+        D = emulgemm.emul_gemm_unequal(A, B, sa, 8, t=sa + 8)
+        errs.append(np.abs(D - ref).max())
+    assert all(errs[i] > errs[i + 1] for i in range(3)), errs

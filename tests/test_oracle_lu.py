@@ -227,3 +227,19 @@ def test_sampled_row_residuals_pinned():
     assert residual.chol_residual_rows(S, L2, [50]) > 1e6
     assert residual.chol_residual_rows(S, L2, [20]) > 1e3
     assert residual.chol_residual_rows(S, L2, [0, 1, 2]) == residual.chol_residual_rows(S, L, [0, 1, 2])
+
+
+@pytest.mark.slow
+def test_fig1_uniform_half_six_fail_seven_pass():
+    """Fig. 1 (Section 6): on HPL-style data A, b ~ U(-1/2, 1/2) the LU solve
+    with 6 splits fails the bar of 16 on the scaled residual of Eq. 8 and
+    with 7 splits passes it (the figure's values are not in the text; its
+    pass/fail outcome is)."""
+    for n in (256, 512):
+        A = inputs.uniform(n, n, seed=n, lo=-0.5, hi=0.5)
+        b = inputs.vector(n, seed=n + 1, lo=-0.5, hi=0.5)
+        res = {}
+        for s in (6, 7):
+            LU, piv, _ = lu.getrf(A, nb=64, update="emulated", s=s)
+            res[s] = residual.scaled_residual(A, lu.getrs(LU, piv, b), b)
+        assert res[6] > 16 and res[7] < 16, (n, res)
