@@ -498,7 +498,7 @@ def run_fig1(args):
     rows = []
     for n in (256, 512, 1024, 2048, 4096, 8192, 16384):
         gen = torch.Generator(device="cuda")
-        gen.manual_seed(n)
+        gen.manual_seed(n + 7919)          # another stream than A's
         A0 = inputs.uniform_device(n, n, seed=n, lo=-0.5, hi=0.5)
         b0 = torch.rand(n, generator=gen, device="cuda", dtype=torch.float64) - 0.5
         row = {"n": n}
