@@ -36,9 +36,10 @@ METRIC_NOPIV = "emulated-FP64 LU without pivoting TFLOP/s on one GB300 at backwa
 METRIC_CHOL = "emulated-FP64 Cholesky TFLOP/s vs native-FP64 Cholesky on one GB300 at backward error ≤16"
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum (673.4 + 516.2 MB) over the algorithmic
+# dram__bytes_read.sum + dram__bytes_write.sum (609.0 + 500.6 MB) of one launch of the
+# product kernel on 8192^2 x 256 at s = 7 (full ncu capture), over the algorithmic
 # bytes of the same launch (C 8192^2 x 16 B + slices 2 x 7 x 8192 x 256 x 2 B)
-TRAFFIC_RATIO = (673.37e6 + 516.18e6) / (8192.0 * 8192.0 * 16.0 + 2 * 7 * 8192 * 256 * 2.0)
+TRAFFIC_RATIO = (609.01e6 + 500.64e6) / (8192.0 * 8192.0 * 16.0 + 2 * 7 * 8192 * 256 * 2.0)
 
 
 def lu_flops(n):
@@ -313,7 +314,7 @@ def run_ours(args, world, rank, local):
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
     achieved = prof["product_tensor_flops"] / (prof["product_ms"] / 1e3) / 1e12 if prof["product_ms"] > 0 else 0.0
     # DRAM traffic per launch: the full ncu capture of the product kernel on
-    # 8192^2 x 256 measured 1.19 GB against 1.13 GB of algorithmic bytes; that
+    # 8192^2 x 256 measured 1.11 GB against 1.13 GB of algorithmic bytes; that
     # ratio scales this run's algorithmic bytes
     traffic = TRAFFIC_RATIO * prof["product_bytes"] / max(1, prof["product_launches"])
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -449,6 +450,71 @@ def run_gemm(args):
                       "config": {"workload": f"emulated DGEMM m=n={n} k={k} s={s}", "pairs": P},
                       "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                                    "frac": ach / peak, "peak_kind": f"bf16 dense burst, {kind}"}}), flush=True)
+
+
+def run_gemm_sweep(args):
+    """Standalone emulated DGEMM sweep: m = n = k in {4096, 8192, 16384} x s in
+    3..8 (C - A B form, one rounding per entry), TFLOP/s of the emulated FP64
+    product and the product kernel's fraction of the measured BF16 burst peak;
+    and, for inputs u 10^e with u ~ U(-1, 1), e ~ U(-r, r), r in {0, 4, 8, 16},
+    the largest error on 32 sampled entries against the exact product (exact
+    rational sums of the FP64 products), in units of k u (|A||B|)_ij."""
+    import torch
+    from fractions import Fraction
+    from paper_2509_23565_gb300 import inputs
+    from paper_2509_23565_gb300.binding import ColMajor, Emul
+    lib = Emul()
+    peaks, kind = measured_peaks()
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    u = 2.0 ** -53
+    rows = []
+    for n in (4096, 8192, 16384):
+        for r in (0, 4, 8, 16):
+            gen = torch.Generator(device="cuda")
+            gen.manual_seed(n * 100 + r)
+            A = ColMajor(inputs.log_scaled_device(n, n, r, gen), n, n)
+            B = ColMajor(inputs.log_scaled_device(n, n, r, gen), n, n)
+            C = ColMajor(torch.zeros((n, n), dtype=torch.float64, device="cuda"), n, n)
+            rng = np.random.default_rng(n + r)
+            samp = [(int(i), int(j)) for i, j in zip(rng.integers(0, n, 32), rng.integers(0, n, 32))]
+            Ah = {i: A.store[:, i].cpu().numpy() for i, _ in samp}        # row i of A (column-major store)
+            Bh = {j: B.store[j].cpu().numpy() for _, j in samp}           # column j of B
+            for s in (3, 4, 5, 6, 7, 8):
+                timed = r == 0 or (n == 4096)
+                if not timed:
+                    continue
+                reps = 3 if n < 16384 else 2
+                lib.dgemm(A, B, C, s, 1.0, 0.0)
+                lib.profile_read()
+                lib.profile_enable(True)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                for _ in range(reps):
+                    lib.dgemm(A, B, C, s, 1.0, 0.0)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                prof = lib.profile_read()
+                lib.profile_enable(False)
+                lib.sync_status()
+                ach = prof["product_tensor_flops"] / (prof["product_ms"] / 1e3) / 1e12
+                Ch = C.store.cpu().numpy().T
+                worst = 0.0
+                for i, j in samp:
+                    a, b = Ah[i], Bh[j]
+                    exact = sum((Fraction(float(x)) * Fraction(float(y)) for x, y in zip(a, b)), Fraction(0))
+                    scale = float(np.abs(a) @ np.abs(b)) * n * u
+                    if scale > 0:
+                        worst = max(worst, abs(float(Fraction(float(Ch[i, j])) - exact)) / scale)
+                rows.append({"n": n, "r": r, "s": s, "ms": ms, "tflops": 2.0 * n ** 3 / (ms / 1e3) / 1e12,
+                             "frac_bf16_burst": ach / peak, "max_err_in_k_u_AB": worst})
+            del A, B, C
+            torch.cuda.empty_cache()
+    print(json.dumps({"metric": "emulated DGEMM sweep (TFLOP/s, roofline fraction, error vs exact)",
+                      "config": {"workload": "m=n=k in {4096, 8192, 16384}, s in 3..8, u 10^e inputs"},
+                      "peak_kind": f"bf16 dense burst, {kind}", "rows": rows}), flush=True)
 
 
 def run_table2(args):
@@ -623,7 +689,7 @@ def main():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="lu",
-                   choices=["lu", "lu_nopiv", "chol", "gemm", "selector", "batched", "table2", "fig1"])
+                   choices=["lu", "lu_nopiv", "chol", "gemm", "gemm_sweep", "selector", "batched", "table2", "fig1"])
     p.add_argument("--range", type=float, default=0.0,
                    help="LU input u 10^e, e ~ U(-range, range) (0: uniform(-1,1))")
     p.add_argument("--cond", type=float, default=1e12, help="condition number of the Cholesky input")
@@ -664,6 +730,9 @@ def main():
         return
     if args.workload == "fig1":
         run_fig1(args)
+        return
+    if args.workload == "gemm_sweep":
+        run_gemm_sweep(args)
         return
     world, rank, local = dist_setup()
     run_ours(args, world, rank, local)
