@@ -207,7 +207,8 @@ int emul_backward_error(emul_handle_t h, int n, const double* A, int lda, const 
  * takes whole systems from a work queue (largest first) and factors them in
  * reduced precision -- FP32 panel with partial pivoting, trailing updates by
  * the split-integer product (Sec. 2, Eq. 2) with `slices` INT8 slices as exact
- * INT8 x INT8 -> INT32 dot products -- then refines in FP64 (residual
+ * INT8 x INT8 -> INT32 tensor-core products recombined in FP64 -- then refines
+ * in FP64 (residual
  * b - A x with the original A) until the backward error
  * ||b - A x|| / (||A|| ||x|| n 2^-53) is at most 1 or max_iter is reached.
  * A system whose refinement has not converged after 8 steps is refactored

@@ -9,8 +9,10 @@
 //      FP32 panel (pivot = first largest |a|), FP32 triangular solve for U12,
 //      trailing update A22 -= L21 U12 emulated with s INT8 slices: per-row /
 //      per-column power-of-two scales, slices of 7 bits, slice pairs with
-//      p + q <= s + 1 as exact INT8 x INT8 -> INT32 dot products (dp4a),
-//      exact integer recombination, one rounding to FP32;
+//      p + q <= s + 1 as exact INT8 x INT8 -> INT32 products on the tensor
+//      cores (warp-level mma.sync m16n8k32 tiles: one system per block does
+//      not fill a 128-wide tcgen05 tile), recombination in FP64, then the
+//      FP32 working copy rounded once;
 //   2. x0 from the FP32 factors; then until the backward error
 //      ||b - A x|| / (||A|| ||x|| n 2^-53) <= target or max_iter: r = b - A x
 //      in FP64 with the original A, d from the FP32 factors, x += d.
@@ -156,9 +158,25 @@ __device__ void lu_solve_f32(const float* W, int n, const int* piv, float* d) {
   }
 }
 
+// Level sums of one 16 x 8 output tile on the tensor cores: D += A B^T with A
+// 16 x 32 and B 8 x 32 signed 8-bit, exact INT32 accumulation
+// (mma.sync m16n8k32; lane l holds rows l/4 and l/4 + 8, columns 2 (l%4) and
+// 2 (l%4) + 1 of the tile, and the A / B bytes k = 4 (l%4) .. +3 and +16 .. +19).
+__device__ __forceinline__ void mma_s8_16x8x32(int (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                               uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t ld_s8x4(const int8_t* p, bool ok) {
+  return ok ? *reinterpret_cast<const uint32_t*>(p) : 0u;
+}
+
 __device__ void factor_system(const BatchSys& S, int s, Scratch& sc, int* info, float* sv, int* si) {
   const int n = S.n, nb = S.nb;
-  const int nb4 = (nb + 3) / 4 * 4;
+  const int nb4 = (nb + 31) / 32 * 32;   // slice row length: whole K steps of 32, zero padded
   float* W = sc.W;
   for (long idx = threadIdx.x; idx < static_cast<long>(n) * n; idx += blockDim.x) {
     const int i = static_cast<int>(idx % n), j = static_cast<int>(idx / n);
@@ -243,28 +261,59 @@ __device__ void factor_system(const BatchSys& S, int s, Scratch& sc, int* info, 
       }
     }
     __syncthreads();
-    // ---- A22 -= D with D = sum_{L <= s+1} I_L 2^(e_i + f_j - 7L): the level sums I_L
-    // are exact INT32 dot products of INT8 slices (dp4a); they are combined in
-    // FP32, the working precision of this factorization
-    const long ms = static_cast<long>(m2) * m2;
-    const int words = nb4 / 4;
-    for (long idx = threadIdx.x; idx < ms; idx += blockDim.x) {
-      const int i = static_cast<int>(idx % m2), j = static_cast<int>(idx / m2);
-      const int ef = sc.ea[i] + sc.fb[j];
-      float D = 0.f;
-      for (int L = s + 1; L >= 2; --L) {
-        int I = 0;
-        for (int pp = 1; pp <= L - 1; ++pp) {
+    // ---- A22 -= D with D = sum_{L <= s+1} I_L 2^(e_i + f_j - 7L): the level sums
+    // I_L are exact INT32 products of INT8 slices on the tensor cores
+    // (mma.sync, one 16 x 8 tile per warp at a time), recombined in FP64: for
+    // s <= 5 the exact sum T = sum_L I_L 2^(7(s+1-L)) (below 2^50) is formed
+    // in int64 and converted once, above that the levels are added in FP64;
+    // the FP32 working copy then takes RN(W - D).
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = lane >> 2, tq = lane & 3;
+    const int tm = (m2 + 15) / 16, tn = (m2 + 7) / 8;
+    const int ksteps = nb4 / 32;
+    const int t = s + 1;
+    for (int tile = warp; tile < tm * tn; tile += kBThreads / 32) {
+      const int i0 = (tile % tm) * 16, c0 = (tile / tm) * 8;
+      const int ra = i0 + g, rb = i0 + g + 8, cb = c0 + g;
+      long long T[4] = {0, 0, 0, 0};
+      double Dd[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int L = 2; L <= t; ++L) {
+        int c[4] = {0, 0, 0, 0};
+        for (int pp = 1; pp <= s; ++pp) {
           const int qq = L - pp;
-          if (pp > s || qq > s) continue;
-          const int* a = reinterpret_cast<const int*>(sc.SA + (static_cast<long>(pp - 1) * n + i) * nb4);
-          const int* bq = reinterpret_cast<const int*>(sc.SB + (static_cast<long>(qq - 1) * n + j) * nb4);
-          for (int w = 0; w < words; ++w) I = __dp4a(a[w], bq[w], I);
+          if (qq < 1 || qq > s) continue;
+          const int8_t* Ap = sc.SA + static_cast<long>(pp - 1) * n * nb4;
+          const int8_t* Bp = sc.SB + static_cast<long>(qq - 1) * n * nb4;
+          for (int kk = 0; kk < ksteps; ++kk) {
+            const int k0 = kk * 32 + tq * 4;
+            const uint32_t a0 = ld_s8x4(Ap + static_cast<long>(ra) * nb4 + k0, ra < m2);
+            const uint32_t a1 = ld_s8x4(Ap + static_cast<long>(rb) * nb4 + k0, rb < m2);
+            const uint32_t a2 = ld_s8x4(Ap + static_cast<long>(ra) * nb4 + k0 + 16, ra < m2);
+            const uint32_t a3 = ld_s8x4(Ap + static_cast<long>(rb) * nb4 + k0 + 16, rb < m2);
+            const uint32_t b0 = ld_s8x4(Bp + static_cast<long>(cb) * nb4 + k0, cb < m2);
+            const uint32_t b1 = ld_s8x4(Bp + static_cast<long>(cb) * nb4 + k0 + 16, cb < m2);
+            mma_s8_16x8x32(c, a0, a1, a2, a3, b0, b1);
+          }
         }
-        if (I) D += ldexpf(static_cast<float>(I), ef - 7 * L);
+        if (s <= 5) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) T[q] = T[q] * 128 + c[q];
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int i = i0 + g + (q >= 2 ? 8 : 0), j = c0 + tq * 2 + (q & 1);
+            if (i < m2 && j < m2 && c[q]) Dd[q] += ldexp(static_cast<double>(c[q]), sc.ea[i] + sc.fb[j] - 7 * L);
+          }
+        }
       }
-      float* cp = W + (j0 + jb + i) + static_cast<long>(j0 + jb + j) * n;
-      *cp = *cp - D;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = i0 + g + (q >= 2 ? 8 : 0), j = c0 + tq * 2 + (q & 1);
+        if (i >= m2 || j >= m2) continue;
+        const double D = s <= 5 ? ldexp(static_cast<double>(T[q]), sc.ea[i] + sc.fb[j] - 7 * t) : Dd[q];
+        float* cp = W + (j0 + jb + i) + static_cast<long>(j0 + jb + j) * n;
+        *cp = static_cast<float>(static_cast<double>(*cp) - D);
+      }
     }
     __syncthreads();
   }

@@ -39,6 +39,10 @@ def test_batched_backward_error(gpu_lib, r, slices):
         assert berr[i] <= 16          # the device's own FP64 residual estimate
         assert np.array_equal(dA[i].numpy(), A)          # A is not modified
     assert iters.max() <= 20
+    if r == 0:
+        # the reduced-slice factors are good preconditioners on U(-1, 1) data:
+        # refinement gains ~7 s - 1 bits per step (a wrong level sum would show here)
+        assert iters.max() <= 6, iters
 
 
 def test_batched_config5_sample(gpu_lib):
