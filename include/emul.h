@@ -70,15 +70,15 @@ size_t emul_workspace_bytes(emul_handle_t handle);
  * 64-column variant, level_sums = 1 the emul_level_sums mode; threshold is
  * the last level kept (0: slices + 1; else 2..2*slices).  Needs no GPU.
  *   sweeps     out, cap_sweeps rows of EMUL_SWEEP_INTS ints:
- *              k0c, k1c (K chunks of 32), L[2], pb[2], pe[2], flags[2], rel[2],
- *              nplanes, kcs (L[1] = 0: one job; flags: 1 open, 2 stash,
- *              4 take, 8 final; rel: jobs from a stash to its take)
+ *              k0c, k1c (K chunks of 32), L[2], pb[2], pe[2], flags[2],
+ *              nplanes, kcs (L[1] = 0: one job; flags: 1 final, the job
+ *              whose term completes the exact sum that is rounded)
  *   table      out, cap_table bytes: slot (bits 0-1) and barrier parity
  *              (bit 2) of job j in tile phase ph at ph * njobs + j
  *   meta       out, 5 ints: nsweeps, njobs, t0, period, table bytes
  * Returns EMUL_OK, EMUL_INVALID_ARG (no schedule for these arguments, or a
  * capacity too small; meta is still filled when a schedule exists). */
-#define EMUL_SWEEP_INTS 14
+#define EMUL_SWEEP_INTS 12
 int emul_schedule(int slices, int k, int wide, int level_sums, int threshold, int* sweeps, int cap_sweeps,
                   unsigned char* table, int cap_table, int* meta);
 

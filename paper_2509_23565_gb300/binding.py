@@ -328,8 +328,7 @@ class Emul:
         return out
 
 
-SWEEP_FIELDS = ("k0c", "k1c", "L0", "L1", "pb0", "pb1", "pe0", "pe1", "flags0", "flags1", "rel0", "rel1",
-                "nplanes", "kcs")
+SWEEP_FIELDS = ("k0c", "k1c", "L0", "L1", "pb0", "pb1", "pe0", "pe1", "flags0", "flags1", "nplanes", "kcs")
 
 
 def schedule(slices, k, wide=False, level_sums=False, t=0):

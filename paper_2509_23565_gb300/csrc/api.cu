@@ -1,5 +1,6 @@
 // C-ABI entry points: handle management, slicing, level sums and the emulated
 // DGEMM (arXiv 2509.23565, Section 2, Eq. 1-4; Section 4, Eq. 7).
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -34,25 +35,23 @@ struct PairSet {
 };
 
 // Sum over the levels L = 2..last of n_L 2^(7(last-L)) times 127^2: the
-// worst-case magnitude per unit of k of the Horner state after level `last`
-// (t - 1 for the narrow variant's state before its final level, t for the
-// wide variant's complete state).
+// worst-case magnitude per unit of k of T = sum_L I_L 2^(7(last-L)) (the
+// wide variant's state after all its jobs, last = t).
 long double horner_bound_per_k(const PairSet& ps, int last) {
   long double acc = 0.0L;
   for (int L = 2; L <= last; ++L) acc = acc * 128.0L + ps.count(L);
   return acc * 127.0L * 127.0L;
 }
 
-
 // K chunks per accumulator job of n slice pairs under the exactness budget.
 int seg_chunks(int n) { return n > 0 ? kExactBudget / (n * kBK) : 0; }
 
 struct Job {
-  int L, pb, pe, c0, c1, flags, rel;
+  int L, pb, pe, c0, c1, flags;
 };
 
-Job make_job(const PairSet& ps, int L, int c0, int c1, int flags, int rel) {
-  return Job{L, ps.lo(L), ps.hi(L), c0, c1, flags, rel};
+Job make_job(const PairSet& ps, int L, int c0, int c1, int flags) {
+  return Job{L, ps.lo(L), ps.hi(L), c0, c1, flags};
 }
 
 void push_sweep(std::vector<Sweep>& out, const Job& a, const Job* b) {
@@ -66,7 +65,6 @@ void push_sweep(std::vector<Sweep>& out, const Job& a, const Job* b) {
     sw.pb[j] = static_cast<int8_t>(js[j]->pb);
     sw.pe[j] = static_cast<int8_t>(js[j]->pe);
     sw.flags[j] = static_cast<int8_t>(js[j]->flags);
-    sw.rel[j] = static_cast<int8_t>(js[j]->rel);
     const int pj = js[j]->pe > js[j]->L - js[j]->pb ? js[j]->pe : js[j]->L - js[j]->pb;
     np = np > pj ? np : pj;
   }
@@ -76,10 +74,15 @@ void push_sweep(std::vector<Sweep>& out, const Job& a, const Job* b) {
 
 // Banded schedule: the levels are covered by bands of one level or of two
 // adjacent levels.  A two-level band (L, L+1) shares every staged chunk
-// between both levels (the planes of L are a subset of those of L+1); when
-// the pair does not fit the exactness budget over the whole K it runs as two
-// K halves, the first half of L+1 stashed until L is complete.  The bands
-// minimise the staged planes per K chunk (dynamic programme over the levels).
+// between both levels (the planes of L are a subset of those of L+1); a band
+// that does not fit the exactness budget over the whole K runs in K groups.  The bands minimise the staged planes per K chunk (dynamic
+// programme over the levels).  The epilogue adds every job's level sum with
+// its weight, R += I_L 2^(7(t-L)), so the jobs may come in any order: the
+// bands are issued from the highest level down, each tile starting with its
+// longest MMA jobs (they keep the tensor cores busy while the epilogue rounds
+// the previous tile) and ending, in the 64-bit variant, with level 2 as one
+// single job: the final job, whose term 2^(7(t-2)) I_2 is added and rounded
+// last.
 bool build_banded(const PairSet& ps, int t, int nch, bool wide, std::vector<Sweep>& out) {
   out.clear();
   const int kInf = 1 << 28;
@@ -88,87 +91,78 @@ bool build_banded(const PairSet& ps, int t, int nch, bool wide, std::vector<Swee
   for (int L = t; L >= 2; --L) {
     cost[L] = kInf;
     const int sg1 = seg_chunks(ps.count(L));
-    if (sg1 >= 1 && cost[L + 1] < kInf && (wide || L < t || groups(sg1) <= 2)) {
+    // the final job (level 2 in the 64-bit variant) must be one job alone
+    if (sg1 >= 1 && cost[L + 1] < kInf && (wide || L > 2 || groups(sg1) == 1)) {
       cost[L] = ps.planes(L) + cost[L + 1];
       choice[L] = 1;
     }
-    if (L + 1 <= t && cost[L + 2] < kInf) {
+    if (L + 1 <= t && cost[L + 2] < kInf && (wide || L > 2)) {
       const int a = seg_chunks(ps.count(L)), b = seg_chunks(ps.count(L + 1));
       const int sg2 = a < b ? a : b;
-      if (sg2 >= 1 && groups(sg2) <= 2 && ps.planes(L + 1) + cost[L + 2] < cost[L]) {
+      if (sg2 >= 1 && ps.planes(L + 1) + cost[L + 2] < cost[L]) {
         cost[L] = ps.planes(L + 1) + cost[L + 2];
         choice[L] = 2;
       }
     }
   }
   if (cost[2] >= kInf) return false;
-  for (int L = 2; L <= t;) {
-    if (choice[L] == 1) {
+  std::vector<std::pair<int, int>> bands;   // (first level, levels)
+  for (int L = 2; L <= t; L += choice[L]) bands.push_back({L, choice[L]});
+  for (auto it = bands.rbegin(); it != bands.rend(); ++it) {
+    const int L = it->first;
+    if (it->second == 1) {
       const int G = groups(seg_chunks(ps.count(L)));
       const int size = (nch + G - 1) / G;
-      const bool fin = !wide && L == t;
       for (int g = 0; g < G; ++g) {
         const int c0 = g * size, c1 = c0 + size < nch ? c0 + size : nch;
-        int flags = g == 0 ? kOpen : 0, rel = 0;
-        if (fin) {
-          if (G == 1) flags = kFinal;
-          else if (g == 0) flags = kStash, rel = 1;
-          else flags = kTake | kFinal;
-        }
-        push_sweep(out, make_job(ps, L, c0, c1, flags, rel), nullptr);
+        push_sweep(out, make_job(ps, L, c0, c1, (!wide && L == 2) ? kFinal : 0), nullptr);
       }
-      L += 1;
     } else {
       const int a = seg_chunks(ps.count(L)), b = seg_chunks(ps.count(L + 1));
       const int G = groups(a < b ? a : b);
-      const bool fin = !wide && L + 1 == t;
-      if (G == 1) {
-        const Job j1 = make_job(ps, L + 1, 0, nch, fin ? kFinal : kOpen, 0);
-        push_sweep(out, make_job(ps, L, 0, nch, kOpen, 0), &j1);
-      } else {
-        const int h = (nch + 1) / 2;
-        const Job j1 = make_job(ps, L + 1, 0, h, kStash, 2);
-        push_sweep(out, make_job(ps, L, 0, h, kOpen, 0), &j1);
-        const Job j2 = make_job(ps, L + 1, h, nch, kTake | (fin ? kFinal : kOpen), 0);
-        push_sweep(out, make_job(ps, L, h, nch, 0, 0), &j2);
+      const int size = (nch + G - 1) / G;
+      for (int g = 0; g < G; ++g) {
+        const int c0 = g * size, c1 = c0 + size < nch ? c0 + size : nch;
+        const Job j1 = make_job(ps, L + 1, c0, c1, 0);
+        push_sweep(out, make_job(ps, L, c0, c1, 0), &j1);
       }
-      L += 2;
     }
   }
   return true;
 }
 
-// Level-ordered schedule: a level whose n_L pairs fit the budget over the whole
-// K is one job; otherwise (narrow variant) its pairs are split into groups that
-// fit, or (wide variant) its K range into segments.  Consecutive jobs of one K
-// range share a sweep.  In the narrow variant the last level's jobs (at most
-// two) form the final sweep.
+// Level-ordered schedule, the fallback: from the highest level down, a level
+// whose n_L pairs fit the budget over the whole K is one job; otherwise its
+// pairs are split into groups that fit (64-bit variant) or its K range into
+// segments (128-bit variant).  Consecutive jobs of one K range share a sweep.
+// In the 64-bit variant level 2 comes last as one job (the final job).
 bool build_levelwise(const PairSet& ps, int t, int nch, bool wide, std::vector<Sweep>& out) {
   out.clear();
-  std::vector<Job> jobs, held;
+  std::vector<Job> jobs;
   const int kc = nch * kBK;
-  for (int L = 2; L <= t; ++L) {
+  for (int L = t; L >= 2; --L) {
     const int pb = ps.lo(L);
     const int pe = ps.hi(L);
     const int n = pe - pb + 1;
-    std::vector<Job>& dst = (!wide && L == t) ? held : jobs;
+    const int fin = (!wide && L == 2) ? kFinal : 0;
     if (n * kc <= kExactBudget) {
-      dst.push_back(Job{L, pb, pe, 0, nch, kOpen, 0});
+      jobs.push_back(Job{L, pb, pe, 0, nch, fin});
     } else if (!wide) {
+      if (fin) return false;
       const int per = kExactBudget / kc;          // pairs per job
       if (per < 1) return false;
       for (int p = pb; p <= pe; p += per)
-        dst.push_back(Job{L, p, p + per - 1 < pe ? p + per - 1 : pe, 0, nch, p == pb ? kOpen : 0, 0});
+        jobs.push_back(Job{L, p, p + per - 1 < pe ? p + per - 1 : pe, 0, nch, 0});
     } else {
       int cm = kExactBudget / (kBK * n);
       if (cm < 1) cm = 1;
-      for (int c0 = 0; c0 < nch; c0 += cm)
-        dst.push_back(Job{L, pb, pe, c0, c0 + cm < nch ? c0 + cm : nch, c0 == 0 ? kOpen : 0, 0});
+      for (int c0 = 0; c0 < nch; c0 += cm) jobs.push_back(Job{L, pb, pe, c0, c0 + cm < nch ? c0 + cm : nch, 0});
     }
   }
-  if (held.size() > 2) return false;
   for (size_t i = 0; i < jobs.size();) {
-    if (i + 1 < jobs.size() && jobs[i + 1].c0 == jobs[i].c0 && jobs[i + 1].c1 == jobs[i].c1) {
+    // the final job stays alone in its sweep
+    if (i + 1 < jobs.size() && !(jobs[i + 1].flags & kFinal) && jobs[i + 1].c0 == jobs[i].c0 &&
+        jobs[i + 1].c1 == jobs[i].c1) {
       push_sweep(out, jobs[i], &jobs[i + 1]);
       i += 2;
     } else {
@@ -176,37 +170,24 @@ bool build_levelwise(const PairSet& ps, int t, int nch, bool wide, std::vector<S
       i += 1;
     }
   }
-  if (held.size() == 1) {
-    held[0].flags = kFinal;
-    push_sweep(out, held[0], nullptr);
-  } else if (held.size() == 2) {
-    held[0].flags = kStash;
-    held[0].rel = 1;
-    held[1].flags = kTake | kFinal;
-    push_sweep(out, held[0], &held[1]);
-  }
   return true;
 }
 
 // TMEM slot of every job.  The MMA issuer and the epilogue follow one rule:
-// a job takes the slot whose current job is released earliest in drain order
-// (ties: lowest slot); a stashed job is released with its kTake partner, any
-// other job when it is drained (in level-sum mode, mode 1, every job is
-// drained at once).  The rule is simulated tile by tile until the slot state
-// (release points relative to the tile, use-count parities) repeats; the
-// table holds the transient tiles and one period.  A sweep may only take
-// slots released by jobs before it, otherwise the schedule is rejected.
-bool plan_slots(const std::vector<Sweep>& sw, bool mode1, std::vector<uint8_t>& tab, int& njobs, int& t0,
-                int& period) {
-  std::vector<int> first_of_job, relo;
+// a job takes the slot whose current job is drained earliest (ties: lowest
+// slot); the epilogue releases a slot when it has drained its job (in
+// level-sum mode every job is drained the same way).  The rule is simulated
+// tile by tile until the slot state (release points relative to the tile,
+// use-count parities) repeats; the table holds the transient tiles and one
+// period.  A sweep may only take slots released by jobs before it, otherwise
+// the schedule is rejected.
+bool plan_slots(const std::vector<Sweep>& sw, std::vector<uint8_t>& tab, int& njobs, int& t0, int& period) {
+  std::vector<int> first_of_job;
   for (const Sweep& w : sw) {
-    const int first = static_cast<int>(relo.size());
-    for (int j = 0; j < 2 && w.L[j]; ++j) {
-      first_of_job.push_back(first);
-      relo.push_back(!mode1 && (w.flags[j] & kStash) ? w.rel[j] : 0);
-    }
+    const int first = static_cast<int>(first_of_job.size());
+    for (int j = 0; j < 2 && w.L[j]; ++j) first_of_job.push_back(first);
   }
-  njobs = static_cast<int>(relo.size());
+  njobs = static_cast<int>(first_of_job.size());
   if (njobs == 0) return false;
   constexpr int kS = 4, kMaxTiles = 64;
   constexpr long long kFree = -(1ll << 40);
@@ -235,7 +216,7 @@ bool plan_slots(const std::vector<Sweep>& sw, bool mode1, std::vector<uint8_t>& 
         if (rel[i] < rel[b]) b = i;
       if (rel[b] >= base + first_of_job[j]) return false;
       tab.push_back(static_cast<uint8_t>(b | ((cnt[b] & 1) << 2)));
-      rel[b] = base + j + relo[j];
+      rel[b] = base + j;
       cnt[b]++;
     }
   }
@@ -256,26 +237,28 @@ void set_chunks_per_stage(int s, std::vector<Sweep>& out) {
 
 // Schedule and slot plan for the levels 2..t (t = 0: the default threshold
 // s + 1 of the method): the banded schedule when it exists and plans, else the
-// level-ordered one.
+// level-ordered one.  The level-sum mode (mode1) drains every job the same
+// way and uses the same schedule.
 // sa, sb: slices of A and of B whose pairs are kept (0: s); s = max(sa, sb)
 // is the split both operands get and the number of planes a stage holds.
 bool build_schedule(int s, int nch, bool wide, bool mode1, std::vector<Sweep>& out, std::vector<uint8_t>& tab,
                     int& njobs, int& t0, int& period, int t = 0, int sa = 0, int sb = 0) {
+  (void)mode1;
   if (sa == 0) sa = s;
   if (sb == 0) sb = s;
   if (t == 0) t = s + 1;
   if (t < 2 || t > sa + sb || (sa > sb ? sa : sb) != s) return false;
   const PairSet ps{sa, sb};
-  if (!(build_banded(ps, t, nch, wide, out) && plan_slots(out, mode1, tab, njobs, t0, period)) &&
-      !(build_levelwise(ps, t, nch, wide, out) && plan_slots(out, mode1, tab, njobs, t0, period)))
+  if (!(build_banded(ps, t, nch, wide, out) && plan_slots(out, tab, njobs, t0, period)) &&
+      !(build_levelwise(ps, t, nch, wide, out) && plan_slots(out, tab, njobs, t0, period)))
     return false;
   set_chunks_per_stage(s, out);
   return true;
 }
 
-// The narrow variant keeps the Horner state in int64 and rounds T = R 2^7 + I
-// on a 64-bit magnitude (a 128-bit path covers |R| >= 2^57): it needs the last
-// level in at most two jobs and |R| well inside int64.
+// The narrow variant keeps the state R in int64 and completes T = R + I_2 2^(7(t-2))
+// in its final job (in 64 bits when the warp's terms allow, else in 128): it
+// needs level 2 in one job and the sum of the other levels inside int64.
 bool narrow_ok(int s, int k, int t = 0, int sa = 0, int sb = 0) {
   if (sa == 0) sa = s;
   if (sb == 0) sb = s;
@@ -286,8 +269,14 @@ bool narrow_ok(int s, int k, int t = 0, int sa = 0, int sb = 0) {
   std::vector<uint8_t> tab;
   int nj, t0, per;
   if (!build_schedule(s, nch, false, false, tmp, tab, nj, t0, per, t, sa, sb)) return false;
-  const long double bound = horner_bound_per_k(PairSet{sa, sb}, t - 1) * static_cast<long double>(nch * kBK);
-  return bound < 4.0e18L;   // < 2^62
+  // R, the sum of the levels 3..t with their weights, stays below 2^61, so
+  // that R + I_2 2^(7(t-2)) fits in 64 bits whenever |I_2| 2^(7(t-2)) <= 2^62
+  // (the epilogue's test; otherwise it adds the term in 128 bits).
+  const PairSet ps{sa, sb};
+  const long double kk = static_cast<long double>(nch * kBK);
+  long double r = 0.0L;
+  for (int L = 3; L <= t; ++L) r += ps.count(L) * 127.0L * 127.0L * kk * powl(2.0L, 7.0L * (t - L));
+  return r < 2305843009213693952.0L;   // 2^61
 }
 
 // The wide variant's complete 128-bit Horner state must stay below 2^126.
@@ -714,8 +703,8 @@ int emul_schedule(int slices, int k, int wide, int level_sums, int threshold, in
     return EMUL_INVALID_ARG;
   for (size_t i = 0; i < v.size(); ++i) {
     const Sweep& w = v[i];
-    const int row[EMUL_SWEEP_INTS] = {w.k0c,      w.k1c,      w.L[0],     w.L[1],   w.pb[0],   w.pb[1],  w.pe[0],
-                                      w.pe[1],    w.flags[0], w.flags[1], w.rel[0], w.rel[1], w.nplanes, w.kcs};
+    const int row[EMUL_SWEEP_INTS] = {w.k0c,   w.k1c,      w.L[0],     w.L[1],    w.pb[0], w.pb[1],
+                                      w.pe[0], w.pe[1],    w.flags[0], w.flags[1], w.nplanes, w.kcs};
     for (int j = 0; j < EMUL_SWEEP_INTS; ++j) sweeps[i * EMUL_SWEEP_INTS + j] = row[j];
   }
   std::memcpy(table, tab.data(), tab.size());

@@ -15,20 +15,16 @@ constexpr int kExactBudget = 1040;       // k * pairs per accumulator: 1040 * 12
 // One sweep of the product schedule: one or two accumulator jobs over the K
 // chunks [k0c, k1c), sharing the staged slice tiles of each chunk.  A job
 // sums the slice pairs (p, L-p), p = pb..pe, of one level L into one TMEM slot.
-// The epilogue takes the jobs in schedule order; flags say what it does with
-// each (Horner state R, level sum I of the job):
-//   kOpen   R <- R * 2^7 before the job is added (first job of a level);
-//   kStash  keep the slot untouched; the next kTake job adds its sum too and
-//           releases both slots (rel = jobs until that kTake job);
-//   kTake   add the stashed job's sum to this job's;
-//   kFinal  T = R * 2^7 + I is rounded and C updated (last job of the narrow variant).
-enum JobFlag : int8_t { kOpen = 1, kStash = 2, kTake = 4, kFinal = 8 };
+// The epilogue takes the jobs in schedule order and adds each job's sum with
+// its weight into the state, R += I 2^(7(t-L)); a job flagged kFinal (the last
+// job of the 64-bit variant) completes T = R + I 2^(7(t-L)), rounds it and
+// updates C.
+enum JobFlag : int8_t { kFinal = 1 };
 struct Sweep {
   int16_t k0c, k1c;    // chunk range
   int8_t L[2];         // job levels (L[1] = 0: one job)
   int8_t pb[2], pe[2]; // pair ranges
   int8_t flags[2];     // JobFlag bits of the two jobs
-  int8_t rel[2];       // kStash: schedule distance to the kTake job
   int8_t nplanes;      // slice planes 1..nplanes of A and of B are staged
   int8_t kcs;          // K chunks per stage (kcs * nplanes <= s tiles of A and of B)
 };

@@ -8,11 +8,13 @@
 // BF16, so every product and every partial sum is an integer; an accumulator
 // never receives more than 1040 * 127^2 < 2^24 in magnitude (the schedule
 // splits K where needed), so the FP32 sums are exact.  The epilogue converts
-// each drained level exactly to an integer and folds it into a Horner state
-// R = R * 2^7 + I_L (int64, or 128-bit for the wide variant); the final value
+// each drained level sum exactly to an integer and adds it with its weight,
+// R += I_L 2^(7(t-L)) (int64, or 128-bit for the wide variant), so the levels
+// may be drained in any order; the schedule issues the longest jobs (the
+// highest levels) first and level 2 last.  The exact value
 // T = sum_L I_L 2^(7(t-L)) is rounded once to FP64,
 //   D = RN(T * 2^(e_i + f_j - 7t)),
-// from two exact parts with one FP64 add, and C = RN(RN(alpha D) + RN(beta C))
+// in integer arithmetic, and C = RN(RN(alpha D) + RN(beta C))
 // is written straight back.  For the Schur update (alpha = -1, beta = 1) the
 // epilogue does not read C: it issues red.global.add.f64 of -D, an FP64 add
 // rounded to nearest that L2 performs, so the C update costs no load latency
@@ -27,8 +29,7 @@
 // first warpgroup gives registers to the epilogue warpgroups (setmaxnreg).  A sweep
 // of one or two jobs shares the staged tiles of a chunk; each job's TMEM slot
 // (and the parity of its barriers) comes from a host-planned slot table, so the
-// issuer fills slots while the epilogue drains others, and a stashed job can
-// hold its slot until its partner is drained.  All waits are bounded.
+// issuer fills slots while the epilogue drains others.  All waits are bounded.
 #include <cstdint>
 #include <type_traits>
 
@@ -53,7 +54,6 @@ constexpr int kMaxStages = kMaxStagesCfg;
 constexpr uint32_t kRowBytes = kBK * 2;     // one K-major row of a staged tile
 constexpr uint32_t kSwizzleCode = kRowBytes == 64 ? 4u : 6u;   // descriptor code of SWIZZLE_64B / _32B
 constexpr int kStatusTimeout = -4;
-constexpr long long kFoldLimit = 1ll << 55;   // |R| below it: R * 2^7 + I fits in 64 bits
 
 template <bool WIDE>
 struct Cfg {
@@ -66,27 +66,20 @@ struct Cfg {
   using State = typename std::conditional<WIDE, __int128, long long>::type;
 };
 
-// v * 2^e2 as a double, exact, for 0 < |v| < 2^53 and a normal result.
-__device__ __forceinline__ double exact_i64(long long v, int e2) {
-  const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
-  const int msb = 63 - __clzll((long long)a);
-  const unsigned long long mant = a << (52 - msb);                  // leading one at bit 52
-  const unsigned long long bits = ((unsigned long long)(msb + e2 + 1022) << 52) + mant;
-  return __longlong_as_double((long long)(bits | (v < 0 ? 0x8000000000000000ull : 0ull)));
+// I 2^w in the state's width (the shift is done unsigned: I may be negative).
+template <typename State>
+__device__ __forceinline__ State shl_state(int I, int w);
+template <>
+__device__ __forceinline__ long long shl_state<long long>(int I, int w) {
+  return (long long)((unsigned long long)(long long)I << w);
+}
+template <>
+__device__ __forceinline__ __int128 shl_state<__int128>(int I, int w) {
+  return (__int128)((unsigned __int128)(__int128)I << w);
 }
 
-// RN(T * 2^sh) for T = R * 2^7 + I (|R| < 2^62, |I| < 2^26): T = A1 2^35 + A0 with
-// |A1| < 2^35 and |A0| < 2^37 both exact in FP64, so one DADD of the two exact
-// parts gives the single correct rounding.  Outside -1022 <= sh <= 950 (parts
-// that could be subnormal or overflow) the integer path is used.
-__device__ __forceinline__ double rn_split(long long R, int I, int sh) {
-  if (sh < -1022 || sh > 950) return rn_scaled((__int128)R * 128 + (__int128)I, sh);
-  const long long A1 = R >> 28;
-  const long long A0 = ((R & ((1ll << 28) - 1)) << 7) + I;
-  const double dh = A1 ? exact_i64(A1, sh + 35) : 0.0;
-  const double dl = A0 ? exact_i64(A0, sh) : 0.0;
-  return __dadd_rn(dh, dl);
-}
+// |I 2^w| <= 2^62 for lim = min(62 - w, 31): I >> lim is 0 or -1 exactly then.
+__device__ __forceinline__ bool term_fits(int I, int lim) { return lim >= 31 || (I >> lim) == (I >> 31); }
 
 // RN(x * 2^sh) for a 64-bit integer x, in integer arithmetic only and without
 // branches (the lanes of a warp hold unrelated values), valid for
@@ -369,8 +362,6 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int c = 0; c < CPT; ++c) R[c] = 0;
       const uint8_t* srow = slot_row(tab, a.slots, tloc);
       int jj = 0;
-      int st_slot = 0;
-      uint32_t st_par = 0;
       bool final_done = false;
       for (int sw = 0; sw < a.nsweeps && ok; ++sw) {
         const Sweep S = sched[sw];
@@ -380,23 +371,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t e = srow[jj];
           const int slot = (int)(e & 3u);
           const uint32_t par = (e >> 2) & 1u;
-          if (a.mode == 0 && (fl & kStash)) {
-            // left in its slot until the kTake job
-            st_slot = slot;
-            st_par = par;
-            continue;
-          }
-          const bool take = a.mode == 0 && (fl & kTake);
-          bool released = false;   // slots already released (final step, 64-bit path)
-          if (aborted(abortp) || !mbar_wait(&slot_full[slot], par, a.wait_limit) ||
-              (take && !mbar_wait(&slot_full[st_slot], st_par, a.wait_limit))) {
+          bool released = false;   // slot already released (final step, 64-bit path)
+          if (aborted(abortp) || !mbar_wait(&slot_full[slot], par, a.wait_limit)) {
             if (!aborted(abortp)) raise_timeout(a, abortp);
             ok = false;
             break;
           }
           tc_fence_after();
           const uint32_t ta = tmem + lane_addr + (uint32_t)(slot * Cf::BN + half * CPT);
-          const uint32_t tb = tmem + lane_addr + (uint32_t)(st_slot * Cf::BN + half * CPT);
+          const int wsh = 7 * (a.t - S.L[j]);     // weight of the level: 2^(7(t-L))
           if (a.mode == 1) {
             // level sums out (exact int32), added so that K segments / pair groups accumulate
             const int L = S.L[j];
@@ -415,46 +398,62 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
             }
           } else if (fl & kFinal) {
-            // final step: T = R * 2^7 + I (I of this job plus the stashed one),
-            // rounded once, C updated in place
+            // final step (64-bit variant): T = R + I 2^wsh, rounded once, C
+            // updated in place.  R, the other levels, stays below 2^61, so T
+            // fits in 64 bits when |I| 2^wsh <= 2^62.  When that holds for the
+            // whole warp (it fails only for rows and columns whose leading
+            // digits are near 127 of one sign along the whole K) the term is
+            // added at once, the slot is released and the rounding runs while
+            // the MMAs of the next tile fill it; otherwise the slot is held,
+            // and the elements over the limit re-read I and round T from 128 bits.
             final_done = true;
             const bool rowok = row < a.M;
-            // When no R of the warp reaches 2^55 (R reaches 2^57 only when whole
-            // rows and columns have leading digits near 127 of one sign), T fits
-            // in 64 bits: the last level is folded into R, both TMEM slots are
-            // released at once, and the rounding runs while the MMAs of the next
-            // tile fill them.  Otherwise T is rounded from its two exact parts.
-            bool fits = !WIDE;
+            const int lim = 62 - wsh < 31 ? 62 - wsh : 31;
+            bool fits = true;
 #pragma unroll
-            for (int c = 0; c < CPT; ++c) fits = fits && R[c] > -kFoldLimit && R[c] < kFoldLimit;
+            for (int c16 = 0; c16 < CPT / 16; ++c16) {
+              uint32_t r[16];
+              tmem_ld16(ta + c16 * 16, r);
+              tmem_ld_wait();
+#pragma unroll
+              for (int q = 0; q < 16; ++q) {
+                const int I = f2i(r[q]);
+                if (term_fits(I, lim))
+                  R[c16 * 16 + q] += shl_state<State>(I, wsh);
+                else
+                  fits = false;
+              }
+            }
             fits = __all_sync(0xFFFFFFFFu, fits);
             if (fits) {
-#pragma unroll
-              for (int c4 = 0; c4 < CPT / 4; ++c4) {
-                uint32_t r0[4], r1[4];
-                tmem_ld4(ta + c4 * 4, r0);
-                if (take) tmem_ld4(tb + c4 * 4, r1);
-                tmem_ld_wait();
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                  R[c4 * 4 + q] = R[c4 * 4 + q] * (State)128 + (State)(f2i(r0[q]) + (take ? f2i(r1[q]) : 0));
-              }
               tc_fence_before();
               __syncwarp();
-              if (lane == 0) {
-                mbar_arrive(&slot_empty[slot]);
-                if (take) mbar_arrive(&slot_empty[st_slot]);
-              }
+              if (lane == 0) mbar_arrive(&slot_empty[slot]);
               released = true;
-              double* cp = a.C + row + (long)col0 * a.ldc;
+            }
+            double* cp = a.C + row + (long)col0 * a.ldc;
 #pragma unroll
-              for (int c = 0; c < CPT; ++c, cp += a.ldc) {
+            for (int c4 = 0; c4 < CPT / 4; ++c4) {
+              uint32_t r[4] = {0u, 0u, 0u, 0u};
+              if (!fits) {            // warp-uniform
+                tmem_ld4(ta + c4 * 4, r);
+                tmem_ld_wait();
+              }
+#pragma unroll
+              for (int q = 0; q < 4; ++q, cp += a.ldc) {
+                const int c = c4 * 4 + q;
                 const int col = col0 + c;
                 const int f = __shfl_sync(0xFFFFFFFFu, fcol[0], c);
                 if (!rowok || col >= a.N || (a.lower && row < col)) continue;
-                const double D = (e_row == kNonFinite || f == kNonFinite)
-                                     ? __longlong_as_double(0x7FF8000000000000ll)
-                                     : rn_sum64((long long)R[c], e_row + f + sh0);
+                const int I = f2i(r[q]);
+                const int sh = e_row + f + sh0;
+                double D;
+                if (e_row == kNonFinite || f == kNonFinite)
+                  D = __longlong_as_double(0x7FF8000000000000ll);
+                else if (fits || term_fits(I, lim))
+                  D = rn_sum64((long long)R[c], sh);
+                else
+                  D = rn_scaled((__int128)R[c] + shl_state<__int128>(I, wsh), sh);
                 if (UPD == kSub)
                   red_add_f64(cp, neg_d(D));
                 else if (UPD == kSet)
@@ -462,70 +461,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                 else
                   *cp = apply_update<UPD>(a, D, needs_c ? *cp : 0.0);
               }
-            } else {
-#pragma unroll
-              for (int c4 = 0; c4 < CPT / 4; ++c4) {
-                uint32_t r0[4], r1[4];
-                tmem_ld4(ta + c4 * 4, r0);
-                if (take) tmem_ld4(tb + c4 * 4, r1);
-                tmem_ld_wait();
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                  const int c = c4 * 4 + q;
-                  const int col = col0 + c;
-                  const int f = __shfl_sync(0xFFFFFFFFu, fcol[0], c);
-                  if (!rowok || col >= a.N || (a.lower && row < col)) continue;
-                  const int I = f2i(r0[q]) + (take ? f2i(r1[q]) : 0);
-                  double D;
-                  if (e_row == kNonFinite || f == kNonFinite)
-                    D = __longlong_as_double(0x7FF8000000000000ll);
-                  else if (WIDE)
-                    D = rn_scaled((__int128)R[c] * 128 + (__int128)I, e_row + f + sh0);
-                  else
-                    D = rn_split((long long)R[c], I, e_row + f + sh0);
-                  double* cp = a.C + row + (long)col * a.ldc;
-                  if (UPD == kSub)
-                    red_add_f64(cp, neg_d(D));
-                  else if (UPD == kSet)
-                    *cp = D;
-                  else
-                    *cp = apply_update<UPD>(a, D, needs_c ? *cp : 0.0);
-                }
-              }
             }
           } else {
-            if (fl & kOpen) {
 #pragma unroll
-              for (int c = 0; c < CPT; ++c) R[c] = R[c] * (State)128;
-            }
-            if (!take) {
+            for (int c16 = 0; c16 < CPT / 16; ++c16) {
+              uint32_t r[16];
+              tmem_ld16(ta + c16 * 16, r);
+              tmem_ld_wait();
 #pragma unroll
-              for (int c16 = 0; c16 < CPT / 16; ++c16) {
-                uint32_t r[16];
-                tmem_ld16(ta + c16 * 16, r);
-                tmem_ld_wait();
-#pragma unroll
-                for (int q = 0; q < 16; ++q) R[c16 * 16 + q] += (State)f2i(r[q]);
-              }
-            } else {
-#pragma unroll
-              for (int c8 = 0; c8 < CPT / 8; ++c8) {
-                uint32_t r[8], r2[8];
-                tmem_ld8(ta + c8 * 8, r);
-                tmem_ld8(tb + c8 * 8, r2);
-                tmem_ld_wait();
-#pragma unroll
-                for (int q = 0; q < 8; ++q) R[c8 * 8 + q] += (State)(f2i(r[q]) + f2i(r2[q]));
-              }
+              for (int q = 0; q < 16; ++q) R[c16 * 16 + q] += shl_state<State>(f2i(r[q]), wsh);
             }
           }
           if (!released) {
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) {
-              mbar_arrive(&slot_empty[slot]);
-              if (take) mbar_arrive(&slot_empty[st_slot]);
-            }
+            if (lane == 0) mbar_arrive(&slot_empty[slot]);
           }
         }
       }

@@ -3,14 +3,14 @@
 
 The level sums I_L = sum_{p+q=L} S_p^A S_q^B of Sec. 2 are accumulated in
 jobs (one level, a pair range, a K range) grouped into sweeps; the epilogue
-folds them by Horner's rule, T = sum_L I_L 2^(7(t-L)).  Checked here for every
+adds each job's sum with its level's weight, T = sum_L I_L 2^(7(t-L)).  Checked here for every
 slice count and a range of k, both variants and both modes:
 * every slice pair (p, q) with p + q <= t and every K chunk is summed
   exactly once (t = s + 1, the method's threshold, and other thresholds
   2 <= t <= 2s down to the full s^2-pair product), and no job exceeds the exact-accumulation budget
   (k_job * pairs <= 1040, so |I| < 2^24 in FP32);
-* the job flags implement Horner's rule: each level's contributions end with
-  weight 2^(7(t-L)) (a missing or extra shift fails);
+* the narrow variant's final job (the one whose term completes T before the
+  rounding) is level 2, alone in the last sweep; the wide variant has none;
 * a sweep stages every plane its pairs use, within the stage's s planes;
 * the slot table drives the MMA/epilogue barrier protocol without deadlock,
   with the parity bit of each job equal to the parity of its slot's use count
@@ -22,7 +22,7 @@ from paper_2509_23565_gb300 import binding
 
 BUDGET = 1040
 KBK = 32
-OPEN, STASH, TAKE, FINAL = 1, 2, 4, 8
+FINAL = 1
 KS = (1, 16, 32, 33, 64, 100, 128, 200, 224, 256, 300, 512, 1000, 2048)
 
 
@@ -40,7 +40,7 @@ def jobs_of(sweeps):
             if w[f"L{j}"] == 0:
                 continue
             out.append({"sweep": si, "L": w[f"L{j}"], "pb": w[f"pb{j}"], "pe": w[f"pe{j}"], "c0": w["k0c"],
-                        "c1": w["k1c"], "flags": w[f"flags{j}"], "rel": w[f"rel{j}"]})
+                        "c1": w["k1c"], "flags": w[f"flags{j}"]})
     return out
 
 
@@ -84,56 +84,35 @@ def test_coverage_budget_planes(s, t):
 
 
 @pytest.mark.parametrize("s,t", ST)
-def test_horner_flags(s, t):
-    """Symbolic epilogue: R holds (level, weight exponent) terms; OPEN shifts by 7,
-    a job adds its level at exponent 0, a stash is added at its take, FINAL is
-    R * 2^7 + I.  Every level must end at exponent 7 (t - L)."""
+def test_final_job(s, t):
+    """The narrow variant rounds after its last job, which must be the only
+    job of level 2 (its term I_2 2^(7(t-2)) is the one the epilogue adds in
+    128 bits when it would overflow 64) and alone in the last sweep; the
+    wide variant rounds after all its jobs and flags none.  The first sweep
+    holds the highest level (the longest jobs start each tile)."""
     for k in KS:
         for wide in (False, True):
             r = get(s, k, wide, False, t)
             if r is None:
                 continue
-            jobs = jobs_of(r[0])
-            R = []          # list of [level, exponent, weight in pairs*chunks]
-            stash = None
-            finals = 0
-            for jb in jobs:
-                amount = (jb["pe"] - jb["pb"] + 1) * (jb["c1"] - jb["c0"])
-                if jb["flags"] & STASH:
-                    assert stash is None
-                    stash = (jb["L"], amount)
-                    continue
-                add = [(jb["L"], amount)]
-                if jb["flags"] & TAKE:
-                    assert stash is not None and stash[0] == jb["L"]
-                    add.append(stash)
-                    stash = None
-                if jb["flags"] & (OPEN | FINAL):
-                    for term in R:
-                        term[1] += 7
-                for L, a in add:
-                    R.append([L, 0, a])
-                if jb["flags"] & FINAL:
-                    finals += 1
-                    assert jb is jobs[-1]
-            assert stash is None
-            assert finals == (0 if wide else 1), (s, k, wide)
-            nch = (k + KBK - 1) // KBK
-            per_level = {}
-            for L, e, a in R:
-                assert e == 7 * (t - L), (s, k, wide, L, e)
-                per_level[L] = per_level.get(L, 0) + a
-            for L in range(2, t + 1):
-                pairs = sum(1 for p in range(1, s + 1) if 1 <= L - p <= s)
-                assert per_level.get(L, 0) == pairs * nch
+            sweeps, _, _ = r
+            jobs = jobs_of(sweeps)
+            finals = [jb for jb in jobs if jb["flags"] & FINAL]
+            if wide:
+                assert not finals, (s, k, t)
+                continue
+            assert len(finals) == 1 and finals[0] is jobs[-1], (s, k, t)
+            assert finals[0]["L"] == 2 and [jb["L"] for jb in jobs].count(2) == 1
+            assert sweeps[-1]["L1"] == 0
+            assert max(sweeps[0]["L0"], sweeps[0]["L1"]) == max(jb["L"] for jb in jobs)
 
 
 @pytest.mark.parametrize("s,t", ST)
 def test_slot_protocol(s, t):
     """Barrier-level simulation over several tiles: the MMA side takes a sweep
     when every slot it needs has been released as often as it was allocated;
-    the epilogue drains jobs in order (a stash waits for its take and is
-    released with it).  The table's parity bit must equal the slot's use count
+    the epilogue drains jobs in order and releases each slot when its job is
+    drained.  The table's parity bit must equal the slot's use count
     parity; the simulation must run to the end (no deadlock)."""
     for k in KS:
         for wide in (False, True):
@@ -151,7 +130,6 @@ def test_slot_protocol(s, t):
                 full = {}            # (tile, job) -> slot, once the MMA has committed it
                 mma = (0, 0)         # (tile, sweep)
                 epi = (0, 0)         # (tile, job)
-                stash = None
                 steps = 0
                 while epi[0] < ntiles:
                     steps += 1
@@ -172,16 +150,7 @@ def test_slot_protocol(s, t):
                             progressed = True
                     tile, j = epi
                     if (tile, j) in full:
-                        jb = jobs[j]
-                        sl = full[(tile, j)]
-                        if not ls and jb["flags"] & STASH:
-                            stash = sl
-                        else:
-                            rel[sl] += 1
-                            if not ls and jb["flags"] & TAKE:
-                                assert stash is not None
-                                rel[stash] += 1
-                                stash = None
+                        rel[full[(tile, j)]] += 1
                         epi = (tile, j + 1) if j + 1 < nj else (tile + 1, 0)
                         progressed = True
                     assert progressed, f"deadlock s={s} k={k} wide={wide} level_sums={ls} at {mma} {epi}"
@@ -189,11 +158,11 @@ def test_slot_protocol(s, t):
 
 def test_lu_schedule_shape():
     """The LU's trailing update (s = 7, k = nb = 256, narrow) uses the banded
-    schedule: levels {2}, {3,4}, {5,6} and {7,8} in K halves, 16 staged planes
-    per K chunk."""
+    schedule: levels {7,8} and {5,6} in K halves, then {3,4}, then {2}, 16
+    staged planes per K chunk."""
     sweeps, _, info = binding.schedule(7, 256)
     levels = [(w["L0"], w["L1"]) for w in sweeps]
-    assert levels == [(2, 0), (3, 4), (5, 6), (5, 6), (7, 8), (7, 8)]
+    assert levels == [(7, 8), (7, 8), (5, 6), (5, 6), (3, 4), (2, 0)]
     nch = 8
     assert sum(w["nplanes"] * (w["k1c"] - w["k0c"]) for w in sweeps) == 16 * nch
     assert info["njobs"] == 11
