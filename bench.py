@@ -260,6 +260,10 @@ def run_ours(args, world, rank, local):
     xb = ColMajor(torch.empty((1, n), dtype=torch.float64, device="cuda"), n, 1)
     lib = Emul()
     stream = torch.cuda.current_stream()
+    if getattr(args, "nb_auto", False):
+        # the library's block-size tuner (one timed factorization per candidate
+        # of a synthetic matrix of this size), before any timed work
+        nb = lib.autotune_nb("chol" if chol else "lu", n, s)
 
     def factor_solve():
         if chol:
@@ -345,6 +349,7 @@ def run_ours(args, world, rank, local):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload,
                    "n": n, "nb": nb, "slices": s, "parallelism": "replicas" if world > 1 else "single",
+                   **({"nb_autotuned": [128, 256, 512]} if getattr(args, "nb_auto", False) else {}),
                    **({"cond": args.cond} if chol else {"range": args.range} if args.range > 0 else {}),
                    "l2": "inputs (8 n^2 bytes) larger than L2; each step restores A from a device copy"},
         "backward_error": float(berr[1]), "scaled_residual_eq8": float(berr[0]), "info": info_v,
@@ -730,7 +735,9 @@ def main():
     p.add_argument("--batch-count", type=int, default=4096)
     p.add_argument("--k", type=int, default=256)
     p.add_argument("--n", type=int, default=32768)
-    p.add_argument("--nb", type=int, default=0, help="block size (0: 256 for lu, 1024 for lu_nopiv)")
+    p.add_argument("--nb", type=int, default=0,
+                   help="block size (0: lu and chol tune it over {128, 256, 512} before the timed region; "
+                        "1024 for lu_nopiv, 256 for the other workloads)")
     p.add_argument("--slices", type=int, default=7)
     p.add_argument("--cpu-n", type=int, default=4096,
                    help="size of the oracle's FP64 factorization sample (Cholesky: twice this)")
@@ -741,6 +748,7 @@ def main():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     args = p.parse_args()
+    args.nb_auto = args.nb == 0 and args.workload in ("lu", "chol")
     if args.nb == 0:
         args.nb = 1024 if args.workload == "lu_nopiv" else 256
     if args.warmup < 3:

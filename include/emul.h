@@ -155,12 +155,27 @@ typedef struct emul_stats {
 } emul_stats;
 
 /* LU with partial pivoting of the n x n matrix A (lda), in place (Section 4,
- * Eq. 5-7): right-looking, block size nb (64..256, multiple of 16; 0 = default
- * 128).  The panel is factored in FP64 (pivot search, swaps, scaling); the
- * triangular solve for U12 and the trailing update use the emulated product
- * with `slices` slices.  ipiv: n int32 (device); info: 1 int32 (device). */
+ * Eq. 5-7): right-looking, block size nb (16..512, multiple of 16; 0 = default
+ * 128; EMUL_NB_AUTO = tuned by emul_autotune_nb).  The panel is factored in FP64 (pivot search, swaps, scaling; a panel
+ * wider than 256 columns as two halves, the right half updated through the
+ * emulated product); the triangular solve for U12 and the trailing update use
+ * the emulated product with `slices` slices.  ipiv: n int32 (device); info: 1
+ * int32 (device). */
 int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int nb, int slices, int32_t* info,
                 emul_stats* stats);
+
+/* Block-size tuner of emul_dgetrf (kind 0) and emul_dpotrf (kind 1), which
+ * the large factorizations use with nb autotuned in {128, 256, 512}: one
+ * factorization of a synthetic n x n matrix (seeded uniform(-1, 1) entries;
+ * for kind 1 symmetric with diagonal n, hence positive definite) is timed at
+ * each candidate with CUDA events on the handle's stream, after one untimed
+ * run, and the fastest is written to *nb_out and kept in the handle for
+ * (kind, n, slices).  nb = EMUL_NB_AUTO in emul_dgetrf / emul_dpotrf takes
+ * the kept value, running this tuner first when there is none.  Allocates
+ * n^2 doubles of device memory for the duration of the call (besides the
+ * factorization's workspace); slices 1..8.  Synchronises the stream. */
+#define EMUL_NB_AUTO (-1)
+int emul_autotune_nb(emul_handle_t h, int kind, int n, int slices, int* nb_out);
 
 /* LU without pivoting of the n x n matrix A (lda), in place, A = L U (L unit
  * lower, U upper): the Level-3-only factorization timed for blocking factors
@@ -184,9 +199,11 @@ int emul_dgetrs(emul_handle_t h, int n, int nrhs, const double* LU, int lda, con
                 int ldb);
 
 /* Lower Cholesky A = L L^T of the symmetric positive definite n x n matrix A
- * (lda), in place; only the lower triangle is read and written.  Diagonal
- * blocks in FP64; L21 = A21 L11^-T and the trailing update (lower tiles only)
- * use the emulated product.  uplo must be 'L'. */
+ * (lda), in place; only the lower triangle is read and written.  Block size
+ * nb (16..512, multiple of 16; 0 = default 128; EMUL_NB_AUTO = tuned by
+ * emul_autotune_nb).  Diagonal blocks in FP64;
+ * L21 = A21 L11^-T and the trailing update (lower tiles only) use the
+ * emulated product.  uplo must be 'L'. */
 int emul_dpotrf(emul_handle_t h, char uplo, int n, double* A, int lda, int nb, int slices, int32_t* info,
                 emul_stats* stats);
 

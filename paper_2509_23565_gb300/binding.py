@@ -17,6 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libemul.so")
 
 EMUL_OK = 0
+NB_AUTO = -1          # EMUL_NB_AUTO: block size from emul_autotune_nb
 STATUS = {0: "EMUL_OK", -1: "EMUL_INVALID_ARG", -2: "EMUL_CUDA_ERROR", -3: "EMUL_NO_WORKSPACE",
           -4: "EMUL_TIMEOUT", -5: "EMUL_NOT_SUPPORTED"}
 
@@ -56,6 +57,7 @@ SIGNATURES = {
     "emul_selector_load": (_c_int, [_vp, ctypes.c_char_p]),
     "emul_dgesv_batched_ir": (_c_int, [_vp, _c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _c_int, _c_int, _c_int]),
     "emul_autotune": (_c_int, [_vp, ctypes.c_char_p]),
+    "emul_autotune_nb": (_c_int, [_vp, _c_int, _c_int, _c_int, _vp]),
     "emul_profile_enable": (_c_int, [_vp, _c_int]),
     "emul_profile_read": (_c_int, [_vp, _vp]),
 }
@@ -210,6 +212,15 @@ class Emul:
     def dgemm_unequal(self, A, B, C, slices_a, slices_b, alpha=1.0, beta=0.0, t=0):
         self._check(self.lib.emul_dgemm_unequal(self.h, C.m, C.n, A.n, alpha, _vp(A.ptr), A.ld, _vp(B.ptr), B.ld,
                                                 beta, _vp(C.ptr), C.ld, slices_a, slices_b, t), "emul_dgemm_unequal")
+
+    def autotune_nb(self, kind, n, slices=7):
+        """Block size of emul_dgetrf (kind "lu") or emul_dpotrf ("chol") for n x n
+        at `slices`, tuned over {128, 256, 512} and kept in the handle (nb=NB_AUTO
+        then uses it)."""
+        out = ctypes.c_int(0)
+        k = {"lu": 0, "chol": 1}[kind]
+        self._check(self.lib.emul_autotune_nb(self.h, k, n, slices, ctypes.byref(out)), "emul_autotune_nb")
+        return out.value
 
     def dgetrf(self, A, nb=0, slices=7, stats=False):
         import torch

@@ -44,6 +44,7 @@ struct emul_handle_s {
   };
   std::vector<PhaseRec> phases;
   std::vector<cudaEvent_t> event_pool;
+  std::map<uint64_t, int> nb_tuned;  // (kind, n, slices) -> block size chosen by emul_autotune_nb
   void* selector = nullptr;         // emul::SelectorState (selector.cu)
   void* batched = nullptr;          // emul::BatchedState (batched.cu)
 };

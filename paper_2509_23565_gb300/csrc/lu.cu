@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(kLeafThreads) getf2_leaf_kernel(double* A, lon
 // src[i], for the *count affected rows (at most 2 (k2-k1)).  Rows k < k2 are
 // final once interchange k is done, so one pass with a small hash of the rows
 // beyond the block suffices.  One thread.
-constexpr int kPermMax = 256;          // interchanges per block (nb <= 256)
+constexpr int kPermMax = 256;          // interchanges per gather map (longer ranges: several maps)
 constexpr int kHash = 1024;
 __global__ void laswp_perm_kernel(const int32_t* ipiv, int k1, int k2, int* map /* [2][2*kPermMax] + count */) {
   __shared__ int cont[kPermMax];                 // content of rows k1..k2-1
@@ -473,6 +473,7 @@ __global__ void gather_rows_kernel(const double* A, long lda, int r0, int n, int
 // warp per column of X (cpb columns per block), lane l holding rows l, l+32,
 // l+64, l+96 in registers, x_k broadcast by shuffle.
 constexpr int kTrsmMax = 128;
+inline int trtri_threads(int nb) { return nb <= 256 ? 256 : 512; }
 __global__ void __launch_bounds__(256) trsm_small_kernel(double* A, long lda, int d0, int w1, int c0, int w2,
                                                          int cpb) {
   // all threads stage L; the first cpb warps solve one column of X each
@@ -641,12 +642,13 @@ __global__ void __launch_bounds__(512) dgemm_nt_small_kernel(int m, int n, int k
 }
 
 // inv (nb x nb, ld nb) <- L^-1 for the lower triangular L at A[d0.., d0..]
-// (unit diagonal if `unit`; nb <= 256): each block solves L x = e_j for the two
+// (unit diagonal if `unit`; nb <= 512, one thread per row: launch with
+// trtri_threads(nb) threads): each block solves L x = e_j for the two
 // columns j and nb - 1 - j (balanced work) by column substitution.  Thread i
 // owns row i of both x's in registers and reads row i of L sixteen columns
 // ahead (coalesced along the column); x_k is published through shared
 // memory, one barrier per step.
-__global__ void __launch_bounds__(256) trtri_cols_kernel(const double* A, long lda, int d0, int nb, int unit,
+__global__ void __launch_bounds__(512) trtri_cols_kernel(const double* A, long lda, int d0, int nb, int unit,
                                                         double* inv, const int32_t* info) {
   __shared__ double bc[2][2];
   if (info && *info != 0) return;
@@ -942,7 +944,7 @@ size_t lu_extra_bytes(int nb, int nsm) {
          al((4ull * kProbeRows + 2ull * nb) * 8) + al(16) + kAl;
 }
 
-// Lower Cholesky of the jb x jb diagonal block at A[d0.., d0..] (jb <= 256),
+// Lower Cholesky of the jb x jb diagonal block at A[d0.., d0..] (jb <= 512),
 // in place, by 32-column panels (chol_leaf_kernel, then the rows below the
 // leaf within the block and the block's trailing lower part by
 // dgemm_nt_small_kernel); with `want_inv`, inv (jb x jb, ld jb) <- L11^-1.
@@ -967,7 +969,7 @@ int chol_diag(emul_handle_t h, double* A, long lda, int d0, int jb, double* inv,
     }
   }
   if (want_inv) {
-    trtri_cols_kernel<<<(jb + 1) / 2, 256, 0, h->stream>>>(A, lda, d0, jb, 0, inv, info);
+    trtri_cols_kernel<<<(jb + 1) / 2, trtri_threads(jb), 0, h->stream>>>(A, lda, d0, jb, 0, inv, info);
     h->launches++;
   }
   return check_cuda(h, cudaGetLastError(), "Cholesky diagonal block");
@@ -1037,11 +1039,17 @@ int laswp_apply(emul_handle_t h, double* A, long lda, int c0, int c1, const int*
   return check_cuda(h, cudaGetLastError(), "laswp");
 }
 
+// The interchanges ipiv[k1..k2) applied in order to columns [c0, c1), at
+// most kPermMax per gather map.
 int laswp(emul_handle_t h, double* A, long lda, int c0, int c1, const int32_t* ipiv, int k1, int k2, int* map) {
   if (c1 <= c0 || k2 <= k1) return EMUL_OK;
-  int rc = laswp_prepare(h, ipiv, k1, k2, map);
-  if (rc) return rc;
-  return laswp_apply(h, A, lda, c0, c1, map);
+  for (int k = k1; k < k2; k += kPermMax) {
+    int rc = laswp_prepare(h, ipiv, k, k + kPermMax < k2 ? k + kPermMax : k2, map);
+    if (rc) return rc;
+    rc = laswp_apply(h, A, lda, c0, c1, map);
+    if (rc) return rc;
+  }
+  return EMUL_OK;
 }
 
 int trsm_small(emul_handle_t h, double* A, long lda, int d0, int w1, int c0, int w2) {
@@ -1074,6 +1082,39 @@ int rgetrf(emul_handle_t h, double* A, long lda, int n, int d0, int w, int pc0, 
                 A + (d0 + w1) + static_cast<long>(d0 + w1) * lda, lda, s, false, 0, nullptr, 0, 0);
   if (rc) return rc;
   return rgetrf(h, A, lda, n, d0 + w1, w2, pc0, pc1, ipiv, info, s, B);
+}
+
+// Panel of width jb at column j0.  Up to kPanelMax columns it is one recursive
+// panel, whose leaves apply each interchange across it.  A wider panel is
+// factored as two such panels: the left one's interchanges are applied to the
+// right one, which is updated (U12 = L11^-1 A12 through the explicit inverse
+// and the emulated product, A22 -= L21 U12) and factored; its interchanges
+// then go back to the left one.  B.inv is free during the panel.
+constexpr int kPanelMax = 256;
+int panel_getrf(emul_handle_t h, double* A, long lda, int n, int j0, int jb, int32_t* ipiv, int32_t* info, int s,
+                const LuBufs& B) {
+  if (jb <= kPanelMax) return rgetrf(h, A, lda, n, j0, jb, j0, j0 + jb, ipiv, info, s, B);
+  const int w1 = kPanelMax, w2 = jb - w1;
+  int rc = rgetrf(h, A, lda, n, j0, w1, j0, j0 + w1, ipiv, info, s, B);
+  if (rc) return rc;
+  rc = laswp(h, A, lda, j0 + w1, j0 + jb, ipiv, j0, j0 + w1, B.map);
+  if (rc) return rc;
+  trtri_cols_kernel<<<(w1 + 1) / 2, trtri_threads(w1), 0, h->stream>>>(A, lda, j0, w1, 1, B.inv, nullptr);
+  h->launches++;
+  rc = check_cuda(h, cudaGetLastError(), "panel trtri");
+  if (rc) return rc;
+  double* A12 = A + j0 + static_cast<long>(j0 + w1) * lda;
+  rc = gemm_run(h, w1, w2, w1, 1.0, Operand{B.inv, 1, w1}, Operand{A12, lda, 1}, 0.0, A12, lda, s, false, 0,
+                nullptr, 0, 0);
+  if (rc) return rc;
+  const int m2 = n - j0 - w1;
+  rc = gemm_run(h, m2, w2, w1, -1.0, Operand{A + (j0 + w1) + static_cast<long>(j0) * lda, 1, lda},
+                Operand{A12, lda, 1}, 1.0, A + (j0 + w1) + static_cast<long>(j0 + w1) * lda, lda, s, false, 0,
+                nullptr, 0, 0);
+  if (rc) return rc;
+  rc = rgetrf(h, A, lda, n, j0 + w1, w2, j0 + w1, j0 + jb, ipiv, info, s, B);
+  if (rc) return rc;
+  return laswp(h, A, lda, j0, j0 + w1, ipiv, j0 + w1, j0 + jb, B.map);
 }
 
 }  // namespace
@@ -1352,13 +1393,119 @@ int getrs_body(emul_handle_t h, int n, int nrhs, const double* LU, int lda, cons
 
 using emul::Operand;
 
+namespace emul {
+namespace {
+
+// Seeded synthetic matrix for the block-size tuner: uniform(-1, 1) from a
+// splitmix64 hash of (seed, i, j); with `spd`, entry (i, j) takes the hash of
+// (max, min) so the matrix is symmetric, and the diagonal is n (strictly
+// diagonally dominant, hence positive definite).
+__global__ void tune_fill_kernel(double* A, int n, int spd, unsigned long long seed) {
+  const long total = static_cast<long>(n) * n;
+  for (long e = blockIdx.x * static_cast<long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long>(gridDim.x) * blockDim.x) {
+    int i = static_cast<int>(e % n), j = static_cast<int>(e / n);
+    if (spd && i == j) {
+      A[e] = static_cast<double>(n);
+      continue;
+    }
+    if (spd && i < j) {
+      const int t = i;
+      i = j;
+      j = t;
+    }
+    unsigned long long z = seed + (static_cast<unsigned long long>(i) * n + j + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    A[e] = static_cast<double>(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  }
+}
+
+uint64_t nb_key(int kind, int n, int slices) {
+  return (static_cast<uint64_t>(kind) << 40) | (static_cast<uint64_t>(slices) << 32) | static_cast<uint32_t>(n);
+}
+
+// nb = EMUL_NB_AUTO: the tuned block size for (kind, n, slices), tuning first
+// when there is none.
+int resolve_nb(emul_handle_t h, int kind, int n, int slices, int* nb) {
+  if (*nb != EMUL_NB_AUTO) return EMUL_OK;
+  const auto it = h->nb_tuned.find(nb_key(kind, n, slices));
+  if (it != h->nb_tuned.end()) {
+    *nb = it->second;
+    return EMUL_OK;
+  }
+  return emul_autotune_nb(h, kind, n, slices, nb);
+}
+
+}  // namespace
+}  // namespace emul
+
 extern "C" {
+
+int emul_autotune_nb(emul_handle_t h, int kind, int n, int slices, int* nb_out) {
+  if (!h) return EMUL_INVALID_ARG;
+  if ((kind != 0 && kind != 1) || n < 1 || slices < 1 || slices > emul::kMaxSlices || !nb_out)
+    return emul::set_error(h, EMUL_INVALID_ARG, "emul_autotune_nb: invalid argument");
+  const int cand[] = {128, 256, 512};
+  double* A = nullptr;
+  int32_t* piv = nullptr;
+  if (cudaMalloc(&A, static_cast<size_t>(n) * n * 8 + static_cast<size_t>(n) * 4 + 256) != cudaSuccess) {
+    cudaGetLastError();
+    return emul::set_error(h, EMUL_NO_WORKSPACE, "emul_autotune_nb: no room for the trial matrix");
+  }
+  piv = reinterpret_cast<int32_t*>(A + static_cast<size_t>(n) * n);
+  int32_t* info = piv + n;
+  const bool prof = h->prof;
+  h->prof = false;   // the trials are not part of any profile
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = emul::check_cuda(h, cudaEventCreate(&e0), "tuner events");
+  if (!rc) rc = emul::check_cuda(h, cudaEventCreate(&e1), "tuner events");
+  // candidates past the first that covers n in one panel change nothing
+  int nc = 1;
+  while (nc < 3 && cand[nc - 1] < n) ++nc;
+  int best = cand[0];
+  float best_ms = 0.0f;
+  // the untimed first run takes the largest candidate: it sizes the workspace
+  // and plans the product schedules the others reuse
+  for (int c = -1; c < nc && !rc; ++c) {
+    const int nb = cand[c < 0 ? nc - 1 : c];
+    emul::tune_fill_kernel<<<4 * h->nsm, 256, 0, h->stream>>>(A, n, kind, 0x5EEDull + static_cast<unsigned>(n));
+    rc = emul::check_cuda(h, cudaGetLastError(), "tuner fill");
+    if (rc) break;
+    cudaEventRecord(e0, h->stream);
+    rc = kind == 0 ? emul_dgetrf(h, n, A, n, piv, nb, slices, info, nullptr)
+                   : emul_dpotrf(h, 'L', n, A, n, nb, slices, info, nullptr);
+    cudaEventRecord(e1, h->stream);
+    if (rc) break;
+    rc = emul::check_cuda(h, cudaEventSynchronize(e1), "tuner run");
+    if (rc) break;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (c >= 0 && (c == 0 || ms < best_ms)) {
+      best_ms = ms;
+      best = nb;
+    }
+  }
+  h->prof = prof;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(A);
+  if (rc) return rc;
+  h->nb_tuned[emul::nb_key(kind, n, slices)] = best;
+  *nb_out = best;
+  return EMUL_OK;
+}
 
 int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int nb, int slices, int32_t* info,
                 emul_stats* stats) {
   if (!h) return EMUL_INVALID_ARG;
+  if (nb == EMUL_NB_AUTO && slices >= 1 && slices <= emul::kMaxSlices && n >= 1) {
+    const int rc = emul::resolve_nb(h, 0, n, slices, &nb);
+    if (rc) return rc;
+  }
   if (nb == 0) nb = 128;
-  if (n < 0 || lda < (n > 1 ? n : 1) || nb < 16 || nb > 256 || nb % 16 != 0 || slices < 0 ||
+  if (n < 0 || lda < (n > 1 ? n : 1) || nb < 16 || nb > 512 || nb % 16 != 0 || slices < 0 ||
       slices > emul::kMaxSlices || (n > 0 && (!A || !ipiv || !info)))
     return emul::set_error(h, EMUL_INVALID_ARG, "emul_dgetrf: invalid argument");
   const bool autos = slices == 0;
@@ -1386,20 +1533,19 @@ int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int n
   for (int j0 = 0; j0 < n; j0 += nb) {
     const int jb = nb < n - j0 ? nb : n - j0;
     int ph = emul::phase_begin(h, EMUL_PHASE_PANEL);
-    rc = emul::rgetrf(h, A, lda, n, j0, jb, j0, j0 + jb, ipiv, info, autos ? s_prev : s_fixed, B);
+    rc = emul::panel_getrf(h, A, lda, n, j0, jb, ipiv, info, autos ? s_prev : s_fixed, B);
     emul::phase_end(h, ph);
     if (rc) return rc;
     ph = emul::phase_begin(h, EMUL_PHASE_SWAP);
-    rc = emul::laswp_prepare(h, ipiv, j0, j0 + jb, B.map);
-    if (rc) return rc;
     // the columns left of the panel get all later interchanges at once, after the loop
-    rc = emul::laswp_apply(h, A, lda, j0 + jb, n, B.map);
+    rc = emul::laswp(h, A, lda, j0 + jb, n, ipiv, j0, j0 + jb, B.map);
     emul::phase_end(h, ph);
     if (rc) return rc;
     const int m2 = n - j0 - jb;
     if (m2 > 0) {
       ph = emul::phase_begin(h, EMUL_PHASE_U12);
-      emul::trtri_cols_kernel<<<(jb + 1) / 2, 256, 0, h->stream>>>(A, lda, j0, jb, 1, B.inv, nullptr);
+      emul::trtri_cols_kernel<<<(jb + 1) / 2, emul::trtri_threads(jb), 0, h->stream>>>(A, lda, j0, jb, 1, B.inv,
+                                                                                          nullptr);
       h->launches++;
       rc = emul::check_cuda(h, cudaGetLastError(), "trtri");
       if (rc) return rc;
@@ -1494,12 +1640,16 @@ int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int n
     h->launches++;
     for (int k = K - 2; k >= 0; --k) {
       const int r0 = (k + 1) * nb, r1 = r0 + nb < n ? r0 + nb : n;
-      rc = emul::laswp_prepare(h, ipiv, r0, r1, B.map);
-      if (rc) return rc;
-      emul::compose_kernel<<<1, 512, 0, h->stream>>>(B.map, G, H);
+      // panel k+1's interchanges, composed from its last gather map back
+      for (int q0 = r0 + (r1 - r0 - 1) / emul::kPermMax * emul::kPermMax; q0 >= r0; q0 -= emul::kPermMax) {
+        rc = emul::laswp_prepare(h, ipiv, q0, q0 + emul::kPermMax < r1 ? q0 + emul::kPermMax : r1, B.map);
+        if (rc) return rc;
+        emul::compose_kernel<<<1, 512, 0, h->stream>>>(B.map, G, H);
+        h->launches++;
+      }
       emul::gather_rows_kernel<<<dim3((n - r0 + 255) / 256, nb), 256, 0, h->stream>>>(A, lda, r0, n, k * nb, G,
                                                                                          tmp);
-      h->launches += 2;
+      h->launches++;
       rc = emul::check_cuda(h,
                             cudaMemcpy2DAsync(A + r0 + static_cast<long>(k) * nb * lda, static_cast<size_t>(lda) * 8,
                                               tmp, static_cast<size_t>(n - r0) * 8, static_cast<size_t>(n - r0) * 8,
@@ -1528,8 +1678,12 @@ int emul_dgetrs(emul_handle_t h, int n, int nrhs, const double* LU, int lda, con
 int emul_dpotrf(emul_handle_t h, char uplo, int n, double* A, int lda, int nb, int slices, int32_t* info,
                 emul_stats* stats) {
   if (!h) return EMUL_INVALID_ARG;
+  if (nb == EMUL_NB_AUTO && slices >= 1 && slices <= emul::kMaxSlices && n >= 1) {
+    const int rc = emul::resolve_nb(h, 1, n, slices, &nb);
+    if (rc) return rc;
+  }
   if (nb == 0) nb = 128;
-  if ((uplo != 'L' && uplo != 'l') || n < 0 || lda < (n > 1 ? n : 1) || nb < 16 || nb > 256 || nb % 16 != 0 ||
+  if ((uplo != 'L' && uplo != 'l') || n < 0 || lda < (n > 1 ? n : 1) || nb < 16 || nb > 512 || nb % 16 != 0 ||
       slices < 1 || slices > emul::kMaxSlices || (n > 0 && (!A || !info)))
     return emul::set_error(h, EMUL_INVALID_ARG, "emul_dpotrf: invalid argument");
   if (stats) *stats = emul_stats{0, slices, slices, 0, 0.0, static_cast<double>(slices)};

@@ -64,6 +64,13 @@ def test_lu_16384_uniform_s7(gpu_lib):
     _lu_check(gpu_lib, inputs.uniform_device(N, N, seed=16001), b, 256, 7, 100)
 
 
+def test_lu_16384_uniform_nb512_s7(gpu_lib):
+    """nb = 512: 512-column panels factored as two halves, trailing updates
+    with k = 512."""
+    b = inputs.vector(N, seed=16004)
+    _lu_check(gpu_lib, inputs.uniform_device(N, N, seed=16003), b, 512, 7, 100)
+
+
 def test_lu_16384_log_scaled_r16_s7(gpu_lib):
     """u 10^e, e ~ U(-16, 16): entries spread over about 106 binades.  Per-row
     and per-column scales keep every update normwise accurate (entries far

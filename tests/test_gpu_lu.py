@@ -16,7 +16,7 @@ import pytest
 
 from oracle import lu as olu, residual
 from paper_2509_23565_gb300 import inputs
-from paper_2509_23565_gb300.binding import ColMajor
+from paper_2509_23565_gb300.binding import NB_AUTO, ColMajor, EmulError
 
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -34,9 +34,13 @@ def _valid_ipiv(ipiv, n):
     return p.shape == (n,) and (p >= np.arange(1, n + 1)).all() and (p <= n).all()
 
 
-@pytest.mark.parametrize("n,nb", [(1, 64), (5, 16), (100, 32), (257, 64), (700, 128), (1024, 64), (1100, 256)])
+@pytest.mark.parametrize("n,nb", [(1, 64), (5, 16), (100, 32), (257, 64), (700, 128), (1024, 64), (1100, 256),
+                                  (600, 384), (1100, 512), (1300, 512)])
 @pytest.mark.parametrize("s", [7, 8])
 def test_getrf_getrs_uniform(gpu_lib, n, nb, s):
+    """Ragged sizes and every block size; panels wider than 256 columns are
+    factored as two halves (384 = 256 + 128; n = 1100 at nb = 512 ends with a
+    76-column panel, n = 1300 with 276 = 256 + 20)."""
     A = inputs.uniform(n, n, seed=10 + n)
     b = inputs.vector(n, seed=20 + n)
     dA, ipiv, info = _factor(gpu_lib, A, nb, s, ld=n + 2)
@@ -149,7 +153,7 @@ def test_multiple_rhs(gpu_lib):
 
 
 @pytest.mark.parametrize("n,nb,cond", [(130, 32, 1e2), (512, 64, 1e8), (1000, 128, 1e12), (1000, 256, 1e8),
-                                       (333, 48, 1e4)])
+                                       (333, 48, 1e4), (1100, 512, 1e8), (700, 320, 1e12)])
 @pytest.mark.parametrize("s", [7, 8])
 def test_potrf_potrs(gpu_lib, n, nb, cond, s):
     A = inputs.spd(n, cond, seed=70 + n)
@@ -182,7 +186,7 @@ def test_potrs_multiple_rhs(gpu_lib):
         assert residual.backward_error(A, X[:, j], B[:, j]) < 16
 
 
-@pytest.mark.parametrize("nb,at", [(32, 150), (256, 300), (256, 45)])
+@pytest.mark.parametrize("nb,at", [(32, 150), (256, 300), (256, 45), (512, 390)])
 def test_potrf_not_spd(gpu_lib, nb, at):
     """A negative diagonal entry makes the leading minor of that order
     non-positive; info is its 1-based index wherever it falls in the blocks
@@ -194,16 +198,44 @@ def test_potrf_not_spd(gpu_lib, nb, at):
     assert int(info.item()) == at + 1
 
 
-@pytest.mark.parametrize("n", [4096])
-def test_getrf_large_backward_error(gpu_lib, n):
+@pytest.mark.parametrize("n,nb", [(4096, 128), (4096, 512)])
+def test_getrf_large_backward_error(gpu_lib, n, nb):
     A = inputs.uniform(n, n, seed=90)
     b = inputs.vector(n, seed=91)
-    dA, ipiv, info = _factor(gpu_lib, A, 128, 7)
+    dA, ipiv, info = _factor(gpu_lib, A, nb, 7)
     assert info == 0 and _valid_ipiv(ipiv, n)
     db = ColMajor.from_numpy(b)
     gpu_lib.dgetrs(dA, ipiv, db)
     x = db.numpy()[:, 0]
     assert residual.backward_error(A, x, b) < 16
+
+
+def test_autotune_nb(gpu_lib):
+    """The block-size tuner picks from {128, 256, 512} (only 128 when one
+    128-column panel covers n), keeps the choice, and nb = NB_AUTO factors
+    with it (LU and Cholesky, checked by the oracle's residuals)."""
+    assert gpu_lib.autotune_nb("lu", 100, 7) == 128
+    n = 700
+    nb = gpu_lib.autotune_nb("lu", n, 7)
+    assert nb in (128, 256, 512)
+    A = inputs.uniform(n, n, seed=95)
+    b = inputs.vector(n, seed=96)
+    dA = ColMajor.from_numpy(A)
+    ipiv, info = gpu_lib.dgetrf(dA, nb=NB_AUTO, slices=7)
+    assert int(info.item()) == 0 and _valid_ipiv(ipiv, n)
+    assert residual.lu_residual(A, dA.numpy(), ipiv.cpu().numpy()) < 100
+    db = ColMajor.from_numpy(b)
+    gpu_lib.dgetrs(dA, ipiv, db)
+    assert residual.backward_error(A, db.numpy()[:, 0], b) < 16
+    # Cholesky: tuned on first use of NB_AUTO
+    S = inputs.spd(600, 1e6, seed=97)
+    dS = ColMajor.from_numpy(S)
+    info = gpu_lib.dpotrf(dS, nb=NB_AUTO, slices=7)
+    assert int(info.item()) == 0
+    assert residual.chol_residual(S, np.tril(dS.numpy())) < 16
+    assert gpu_lib.autotune_nb("chol", 600, 7) in (128, 256, 512)
+    with pytest.raises(EmulError):
+        gpu_lib.autotune_nb("lu", 0, 7)
 
 
 def test_profile_phases(gpu_lib):
