@@ -470,10 +470,13 @@ int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Oper
   rc = get_schedule(h, s, t, nch, wide, mode == 1, &sched, &nsweeps, &plan, s_a, s_b);
   if (rc) return rc;
   const int BN = wide ? 64 : 128;
+  // CTA pairs (cta_group::2) for the 128-column tile once there are two
+  // 128-row tiles: each SM stages half of B, a quarter less than alone
+  const bool pair = !wide && m > 128 && h->nsm >= 2;
   CUtensorMap tmA, tmB;
   rc = encode_slices_map(h, &tmA, sa, m, k, kp, s, 128);
   if (rc) return rc;
-  rc = encode_slices_map(h, &tmB, sb, n, k, kp, s, BN);
+  rc = encode_slices_map(h, &tmB, sb, n, k, kp, s, pair ? BN / 2 : BN);
   if (rc) return rc;
 
   GemmArgs a{};
@@ -491,11 +494,16 @@ int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Oper
   a.sched = sched;
   a.nsweeps = nsweeps;
   a.slots = plan;
-  a.tiles_m = (m + 127) / 128;
+  a.tiles_m = pair ? (m + 255) / 256 : (m + 127) / 128;
   a.tiles_n = (n + BN - 1) / BN;
   a.lower = lower ? 1 : 0;
   a.tri = (lower && !wide && m == n) ? 1 : 0;
-  a.ntiles = a.tri ? a.tiles_m * (a.tiles_m + 1) / 2 : a.tiles_m * a.tiles_n;
+  if (!a.tri)
+    a.ntiles = a.tiles_m * a.tiles_n;
+  else if (!pair)
+    a.ntiles = a.tiles_m * (a.tiles_m + 1) / 2;
+  else   // row pair r < tiles_m - 1 holds 2r + 2 tiles reaching the diagonal, the last one tiles_n
+    a.ntiles = (a.tiles_m - 1) * a.tiles_m + a.tiles_n;
   a.mode = mode;
   a.levels = levels;
   a.ldl = ldl;
@@ -503,13 +511,14 @@ int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Oper
   a.status = h->d_status;
   a.wait_limit = h->wait_limit;
 
-  const size_t stage = gemm_stage_bytes(wide, s);
+  const size_t stage = gemm_stage_bytes(wide, s, pair);
   const size_t budget = 232448 - 1024 - 2048;
   int stages = static_cast<int>(budget / stage);
   if (stages > kMaxStagesCfg) stages = kMaxStagesCfg;
   if (stages < 2) return set_error(h, EMUL_NOT_SUPPORTED, "slice tiles do not fit in shared memory");
   const size_t smem = stages * stage + 1024;
-  const int grid = a.ntiles < h->nsm ? a.ntiles : h->nsm;
+  const int units = pair ? h->nsm / 2 : h->nsm;   // CTAs, or CTA pairs
+  const int grid = (a.ntiles < units ? a.ntiles : units) * (pair ? 2 : 1);
   emul_handle_s::ProfRec rec{};
   if (h->prof) {
     for (int i = 0; i < 2; ++i) {
@@ -530,7 +539,7 @@ int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Oper
     rec.bytes = cells * (beta != 0.0 ? 16.0 : 8.0) + static_cast<double>(s) * 2.0 * k * (m + (same ? 0 : n));
     cudaEventRecord(rec.e0, h->stream);
   }
-  rc = check_cuda(h, launch_gemm(h->stream, wide, tmA, tmB, a, grid, stages, smem), "gemm kernel");
+  rc = check_cuda(h, launch_gemm(h->stream, wide, pair, tmA, tmB, a, grid, stages, smem), "gemm kernel");
   h->launches++;
   if (h->prof) {
     cudaEventRecord(rec.e1, h->stream);
@@ -912,11 +921,11 @@ extern "C" int emul_dgemm_noalloc(void* stream, int m, int n, int k, double alph
   a.ntiles = a.tiles_m * a.tiles_n;
   a.status = status;
   a.wait_limit = 2000000000LL;
-  const size_t stage = gemm_stage_bytes(wide, slices);
+  const size_t stage = gemm_stage_bytes(wide, slices, false);
   int stages = static_cast<int>((232448 - 1024 - 2048) / stage);
   if (stages > kMaxStagesCfg) stages = kMaxStagesCfg;
   if (stages < 2) return EMUL_NOT_SUPPORTED;
   const int grid = a.ntiles < d->nsm ? a.ntiles : d->nsm;
-  return launch_gemm(st, wide, tmA, tmB, a, grid, stages, stages * stage + 1024) == cudaSuccess ? EMUL_OK
+  return launch_gemm(st, wide, false, tmA, tmB, a, grid, stages, stages * stage + 1024) == cudaSuccess ? EMUL_OK
                                                                                              : EMUL_CUDA_ERROR;
 }

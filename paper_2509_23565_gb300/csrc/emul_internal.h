@@ -61,9 +61,11 @@ struct GemmArgs {
 cudaError_t launch_split(cudaStream_t st, int rows, int k, const double* X, long rs, long cs, int s, int32_t* exps,
                          uint16_t* out, long ldk);
 
-// BN = 128 with int64 Horner state (wide = false) or BN = 64 with 128-bit state (wide = true).
-cudaError_t launch_gemm(cudaStream_t st, bool wide, const CUtensorMap& tmA, const CUtensorMap& tmB,
+// BN = 128 with an int64 state (wide = false) or BN = 64 with a 128-bit state
+// (wide = true).  pair (128-column tile only): clusters of two CTAs, tiles of
+// 256 rows (args.tiles_m counts them), tmB staged BN/2 rows per CTA, grid even.
+cudaError_t launch_gemm(cudaStream_t st, bool wide, bool pair, const CUtensorMap& tmA, const CUtensorMap& tmB,
                         const GemmArgs& args, int grid, int stages, size_t smem_bytes);
-size_t gemm_stage_bytes(bool wide, int s);
+size_t gemm_stage_bytes(bool wide, int s, bool pair);
 
 }  // namespace emul

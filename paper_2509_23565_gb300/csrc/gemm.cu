@@ -31,7 +31,10 @@
 // (and the parity of its barriers) comes from a host-planned slot table, so the
 // issuer fills slots while the epilogue drains others.  All waits are bounded.
 #include <cstdint>
+#include <map>
+#include <mutex>
 #include <type_traits>
+#include <utility>
 
 #include "emul_internal.h"
 #include "ptx.cuh"
@@ -152,6 +155,28 @@ __device__ __forceinline__ void tile_coords(const GemmArgs& a, int tile, int& tm
   }
 }
 
+// Tiles of a CTA pair: 256 rows (128 per CTA) x BN columns; tiles_m counts
+// 256-row tiles.  The lower-triangular enumeration keeps the tiles that reach
+// the diagonal: row pair r holds min(2r + 2, tiles_n) of them.
+__device__ __forceinline__ void tile_coords_pair(const GemmArgs& a, int tile, int& tm, int& tn) {
+  if (a.tri) {
+    const int full = (a.tiles_m - 1) * a.tiles_m;   // row pairs before the last: r (r + 1) tiles before row pair r
+    if (tile >= full) {
+      tm = a.tiles_m - 1;
+      tn = tile - full;
+      return;
+    }
+    int r = (int)((sqrtf(4.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
+    while ((long)r * (r + 1) > tile) --r;
+    while ((long)(r + 1) * (r + 2) <= tile) ++r;
+    tm = r;
+    tn = tile - r * (r + 1);
+  } else {
+    tm = tile % a.tiles_m;
+    tn = tile / a.tiles_m;
+  }
+}
+
 __device__ __forceinline__ bool aborted(volatile int* flag) { return *flag != 0; }
 
 // Slot-table row of the i-th tile of this CTA.
@@ -167,12 +192,20 @@ __device__ __forceinline__ void raise_timeout(const GemmArgs& a, volatile int* f
 
 }  // namespace
 
-template <bool WIDE, int UPD>
+// PAIR: a cluster of two CTAs per tile of 256 x BN (cta_group::2).  Each
+// CTA stages its 128 rows of A and BN/2 rows of B; both CTAs' copies complete
+// on rank 0's stage barrier; rank 0's MMA warps issue M = 256 MMAs whose
+// commits reach both CTAs; each CTA drains its own TMEM and both release a
+// slot on rank 0's barrier.  Rank 1's MMA warps stay idle.
+template <bool WIDE, int UPD, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs a,
                 int stages) {
+  static_assert(!(WIDE && PAIR), "CTA pairs use the 128-column tile");
   using Cf = Cfg<WIDE>;
   using State = typename Cf::State;
+  constexpr uint32_t B_T = PAIR ? Cf::B_TILE / 2 : Cf::B_TILE;   // bytes of one staged B plane
+  constexpr int G = PAIR ? 2 : 1;                                  // CTAs per tile
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t stage_full[kMaxStages], stage_empty[kMaxStages];
@@ -184,8 +217,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int s = a.s;
-  const uint32_t stage_bytes = (uint32_t)s * (Cf::A_TILE + Cf::B_TILE);
+  const uint32_t stage_bytes = (uint32_t)s * (Cf::A_TILE + B_T);
   volatile int* abortp = &abort_flag;
+  const uint32_t rank = PAIR ? cluster_rank() : 0u;
+  const int cta0 = (int)blockIdx.x / G, ncta = (int)gridDim.x / G;   // tile loop over CTAs or CTA pairs
 
   const bool sched_in_smem = a.nsweeps <= kSchedSmem;
   if (sched_in_smem)
@@ -203,15 +238,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int i = 0; i < kSlots; ++i) {
       mbar_init(&slot_full[i], 1);
-      mbar_init(&slot_empty[i], kEpiWarps);
+      mbar_init(&slot_empty[i], G * kEpiWarps);
     }
     for (int i = 0; i < kMmaWarps; ++i) mbar_init(&mma_done[i], 1);
     abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == 1) tmem_alloc(&tmem_base, Cf::TMEM_COLS);
+  if (warp == 1) {
+    if (PAIR)
+      tmem_alloc_pair(&tmem_base, Cf::TMEM_COLS);
+    else
+      tmem_alloc(&tmem_base, Cf::TMEM_COLS);
+  }
   tc_fence_before();
   __syncthreads();
+  if (PAIR) cluster_sync();   // barriers of both CTAs initialised before any copy or arrival
   tc_fence_after();
   const uint32_t tmem = tmem_base;
 
@@ -227,10 +268,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
     long it = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+    for (int tile = cta0; tile < a.ntiles && ok; tile += ncta) {
       int tm, tn;
-      tile_coords(a, tile, tm, tn);
-      const int m0 = tm * Cf::BM, n0 = tn * Cf::BN;
+      if (PAIR)
+        tile_coords_pair(a, tile, tm, tn);
+      else
+        tile_coords(a, tile, tm, tn);
+      const int m0 = (tm * G + (int)rank) * Cf::BM, n0 = tn * Cf::BN + (int)rank * (Cf::BN / G);
       for (int sw = 0; sw < a.nsweeps && ok; ++sw) {
         const Sweep S = sched[sw];
         const int np = S.nplanes;
@@ -244,31 +288,46 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           uint8_t* base = smem + (size_t)st * stage_bytes;
-          mbar_arrive_expect_tx_elect(&stage_full[st], (uint32_t)(nu * np) * (Cf::A_TILE + Cf::B_TILE));
-          for (int u = 0; u < nu; ++u)
-            for (int p = 0; p < np; ++p) {
-              const int t = u * np + p;
-              tma_load_3d_elect(base + t * Cf::A_TILE, &tmA, &stage_full[st], (kc + u) * kBK, m0, p);
-              tma_load_3d_elect(base + s * Cf::A_TILE + t * Cf::B_TILE, &tmB, &stage_full[st], (kc + u) * kBK, n0,
-                                p);
-            }
+          if (!PAIR) {
+            mbar_arrive_expect_tx_elect(&stage_full[st], (uint32_t)(nu * np) * (Cf::A_TILE + B_T));
+            for (int u = 0; u < nu; ++u)
+              for (int p = 0; p < np; ++p) {
+                const int t = u * np + p;
+                tma_load_3d_elect(base + t * Cf::A_TILE, &tmA, &stage_full[st], (kc + u) * kBK, m0, p);
+                tma_load_3d_elect(base + s * Cf::A_TILE + t * B_T, &tmB, &stage_full[st], (kc + u) * kBK, n0, p);
+              }
+          } else {
+            // rank 0's barrier counts the bytes of both CTAs (a copy of rank 1
+            // may land before rank 0 announces them: the phase still waits for
+            // rank 0's arrival)
+            if (rank == 0)
+              mbar_arrive_expect_tx_elect(&stage_full[st], (uint32_t)(G * nu * np) * (Cf::A_TILE + B_T));
+            const uint32_t bar0 = mapa_rank(&stage_full[st], 0);
+            for (int u = 0; u < nu; ++u)
+              for (int p = 0; p < np; ++p) {
+                const int t = u * np + p;
+                tma_load_3d_pair_elect(base + t * Cf::A_TILE, &tmA, bar0, (kc + u) * kBK, m0, p);
+                tma_load_3d_pair_elect(base + s * Cf::A_TILE + t * B_T, &tmB, bar0, (kc + u) * kBK, n0, p);
+              }
+          }
         }
       }
     }
-    if (!ok) {
+    if (!ok && rank == 0) {
       // wait (bounded) for the copies still in flight before the block exits
+      // (a pair's copies all complete on rank 0's barriers)
       for (long j = (it - stages > 0 ? it - stages : 0); j < it; ++j)
         mbar_wait(&stage_full[j % stages], (uint32_t)((j / stages) & 1), a.wait_limit / 8);
     }
-  } else if (warp >= 1 && warp <= kMmaWarps) {
+  } else if (warp >= 1 && warp <= kMmaWarps && rank == 0) {
     // ------------------------------------------------------------ MMA issuers
     // the whole warp runs the loop (warp-uniform values); one elected lane issues
     const int myj = warp - 1;   // job of each sweep issued by this warp
     {
-      constexpr uint32_t idesc = idesc_bf16_f32(128, Cf::BN);
+      constexpr uint32_t idesc = idesc_bf16_f32(128 * G, Cf::BN);
       long it = 0, tloc = 0;
       bool ok = true;
-      for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x, ++tloc) {
+      for (int tile = cta0; tile < a.ntiles && ok; tile += ncta, ++tloc) {
         const uint8_t* srow = slot_row(tab, a.slots, tloc);
         int jj = 0;
         for (int sw = 0; sw < a.nsweeps && ok; ++sw) {
@@ -281,7 +340,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t e = srow[jj + myj];
             slot = (int)(e & 3u);
             dcol = tmem + (uint32_t)(slot * Cf::BN);
-            if (aborted(abortp) || !mbar_wait_warp(&slot_empty[slot], ((e >> 2) & 1u) ^ 1u, a.wait_limit)) {
+            const uint32_t spar = ((e >> 2) & 1u) ^ 1u;
+            if (aborted(abortp) || !(PAIR ? mbar_wait_cluster_warp(&slot_empty[slot], spar, a.wait_limit)
+                                          : mbar_wait_warp(&slot_empty[slot], spar, a.wait_limit))) {
               if (!aborted(abortp) && lane == 0) raise_timeout(a, abortp);
               ok = false;
               break;
@@ -312,23 +373,38 @@ __global__ void __launch_bounds__(kThreads, 1)
               for (int p = pb; p <= pe; ++p) {
                 const int q = L - p;
                 const uint64_t da = dA0 + (uint64_t)((u * np + p - 1) * (Cf::A_TILE >> 4));
-                const uint64_t db = dB0 + (uint64_t)((u * np + q - 1) * (Cf::B_TILE >> 4));
+                const uint64_t db = dB0 + (uint64_t)((u * np + q - 1) * (B_T >> 4));
 #pragma unroll
                 for (int kk = 0; kk < kBK / 16; ++kk) {
                   const uint32_t acc = (!first || p != pb || kk != 0) ? 1u : 0u;
-                  mma_bf16_elect(dcol, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, acc);
+                  if (PAIR)
+                    mma_bf16_pair_elect(dcol, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, acc);
+                  else
+                    mma_bf16_elect(dcol, da + (uint64_t)(kk * 2), db + (uint64_t)(kk * 2), idesc, acc);
                 }
               }
             }
-            mma_commit_elect(&stage_empty[st]);   // also by a warp without a job here: the stage needs both
+            // also by a warp without a job here: the stage needs both
+            if (PAIR)
+              mma_commit_pair_both_elect(&stage_empty[st]);
+            else
+              mma_commit_elect(&stage_empty[st]);
           }
           if (!ok) break;
-          if (mine) mma_commit_elect(&slot_full[slot]);
+          if (mine) {
+            if (PAIR)
+              mma_commit_pair_both_elect(&slot_full[slot]);
+            else
+              mma_commit_elect(&slot_full[slot]);
+          }
           jj += nj;
         }
       }
       // every MMA issued by this warp must be complete before TMEM is released
-      mma_commit_elect(&mma_done[myj]);
+      if (PAIR)
+        mma_commit_pair_both_elect(&mma_done[myj]);
+      else
+        mma_commit_elect(&mma_done[myj]);
       mbar_wait(&mma_done[myj], 0, a.wait_limit);
     }
   }
@@ -346,10 +422,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     State R[CPT];
     long tloc = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x, ++tloc) {
+    // rank 0's slot barriers, where both CTAs of a pair release a slot
+    uint32_t slot_empty0 = 0;
+    if (PAIR) slot_empty0 = mapa_rank(&slot_empty[0], 0);
+    auto release = [&](int slot) {
+      if (PAIR)
+        mbar_arrive_cluster(slot_empty0 + (uint32_t)(slot * 8));
+      else
+        mbar_arrive(&slot_empty[slot]);
+    };
+    for (int tile = cta0; tile < a.ntiles && ok; tile += ncta, ++tloc) {
       int tm, tn;
-      tile_coords(a, tile, tm, tn);
-      const int row = tm * Cf::BM + row_t;
+      if (PAIR)
+        tile_coords_pair(a, tile, tm, tn);
+      else
+        tile_coords(a, tile, tm, tn);
+      const int row = (tm * G + (int)rank) * Cf::BM + row_t;
       const int col0 = tn * Cf::BN + half * CPT;
       const int e_row = row < a.M ? a.ea[row] : 0;
       // column scales of this thread's CPT columns, one per lane (broadcast by shuffle)
@@ -428,7 +516,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (fits) {
               tc_fence_before();
               __syncwarp();
-              if (lane == 0) mbar_arrive(&slot_empty[slot]);
+              if (lane == 0) release(slot);
               released = true;
             }
             double* cp = a.C + row + (long)col0 * a.ldc;
@@ -475,7 +563,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!released) {
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&slot_empty[slot]);
+            if (lane == 0) release(slot);
           }
         }
       }
@@ -505,44 +593,91 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
+  if (PAIR) cluster_sync();   // neither CTA leaves while the other may still use its barriers or TMEM
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, Cf::TMEM_COLS);
+    if (PAIR)
+      tmem_dealloc_pair(tmem, Cf::TMEM_COLS);
+    else
+      tmem_dealloc(tmem, Cf::TMEM_COLS);
   }
 }
 
-size_t gemm_stage_bytes(bool wide, int s) {
+size_t gemm_stage_bytes(bool wide, int s, bool pair) {
   return wide ? (size_t)s * (Cfg<true>::A_TILE + Cfg<true>::B_TILE)
-              : (size_t)s * (Cfg<false>::A_TILE + Cfg<false>::B_TILE);
+              : (size_t)s * (Cfg<false>::A_TILE + (pair ? Cfg<false>::B_TILE / 2 : Cfg<false>::B_TILE));
 }
 
-template <bool WIDE, int UPD>
+template <bool WIDE, int UPD, bool PAIR>
 cudaError_t launch_one(cudaStream_t st, const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& args, int grid,
                        int stages, size_t smem_bytes) {
   // The register hand-over between warpgroups is only valid if the block is
   // launched with exactly kLaunchRegs registers per thread.
+  auto kern = gemm_kernel<WIDE, UPD, PAIR>;
   cudaFuncAttributes fa;
-  cudaError_t e = cudaFuncGetAttributes(&fa, (const void*)gemm_kernel<WIDE, UPD>);
+  cudaError_t e = cudaFuncGetAttributes(&fa, (const void*)kern);
   if (e != cudaSuccess) return e;
   if (fa.numRegs != kLaunchRegs) return cudaErrorInvalidConfiguration;
-  e = cudaFuncSetAttribute(gemm_kernel<WIDE, UPD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
   if (e != cudaSuccess) return e;
-  gemm_kernel<WIDE, UPD><<<grid, kThreads, smem_bytes, st>>>(tmA, tmB, args, stages);
-  return cudaGetLastError();
+  if (!PAIR) {
+    kern<<<grid, kThreads, smem_bytes, st>>>(tmA, tmB, args, stages);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem_bytes;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  // the persistent grid holds no more pairs than can be resident at once (an
+  // SM left without a partner would otherwise run its pair after the others)
+  static std::mutex mu;
+  static std::map<std::pair<int, size_t>, int> resident;   // (device, shared memory) -> pairs
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int pairs = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_pair(dev, smem_bytes);
+    const auto it = resident.find(key);
+    if (it != resident.end()) {
+      pairs = it->second;
+    } else {
+      e = cudaOccupancyMaxActiveClusters(&pairs, kern, &cfg);
+      if (e != cudaSuccess) return e;
+      resident[key] = pairs;
+    }
+  }
+  if (pairs < 1) return cudaErrorInvalidConfiguration;
+  if (grid > 2 * pairs) cfg.gridDim = dim3(2 * pairs);
+  return cudaLaunchKernelEx(&cfg, kern, tmA, tmB, args, stages);
 }
 
-cudaError_t launch_gemm(cudaStream_t st, bool wide, const CUtensorMap& tmA, const CUtensorMap& tmB,
+cudaError_t launch_gemm(cudaStream_t st, bool wide, bool pair, const CUtensorMap& tmA, const CUtensorMap& tmB,
                         const GemmArgs& args, int grid, int stages, size_t smem_bytes) {
   const int upd = (args.alpha == -1.0 && args.beta == 1.0) ? kSub
                   : (args.alpha == 1.0 && args.beta == 0.0) ? kSet : kGeneral;
   if (wide) {
-    if (upd == kSub) return launch_one<true, kSub>(st, tmA, tmB, args, grid, stages, smem_bytes);
-    if (upd == kSet) return launch_one<true, kSet>(st, tmA, tmB, args, grid, stages, smem_bytes);
-    return launch_one<true, kGeneral>(st, tmA, tmB, args, grid, stages, smem_bytes);
+    if (upd == kSub) return launch_one<true, kSub, false>(st, tmA, tmB, args, grid, stages, smem_bytes);
+    if (upd == kSet) return launch_one<true, kSet, false>(st, tmA, tmB, args, grid, stages, smem_bytes);
+    return launch_one<true, kGeneral, false>(st, tmA, tmB, args, grid, stages, smem_bytes);
   }
-  if (upd == kSub) return launch_one<false, kSub>(st, tmA, tmB, args, grid, stages, smem_bytes);
-  if (upd == kSet) return launch_one<false, kSet>(st, tmA, tmB, args, grid, stages, smem_bytes);
-  return launch_one<false, kGeneral>(st, tmA, tmB, args, grid, stages, smem_bytes);
+  if (pair) {
+    if (upd == kSub) return launch_one<false, kSub, true>(st, tmA, tmB, args, grid, stages, smem_bytes);
+    if (upd == kSet) return launch_one<false, kSet, true>(st, tmA, tmB, args, grid, stages, smem_bytes);
+    return launch_one<false, kGeneral, true>(st, tmA, tmB, args, grid, stages, smem_bytes);
+  }
+  if (upd == kSub) return launch_one<false, kSub, false>(st, tmA, tmB, args, grid, stages, smem_bytes);
+  if (upd == kSet) return launch_one<false, kSet, false>(st, tmA, tmB, args, grid, stages, smem_bytes);
+  return launch_one<false, kGeneral, false>(st, tmA, tmB, args, grid, stages, smem_bytes);
 }
 
 }  // namespace emul
