@@ -520,6 +520,24 @@ __global__ void __launch_bounds__(kThreads, 1)
               released = true;
             }
             double* cp = a.C + row + (long)col0 * a.ldc;
+            // a warp whose rows and columns are all inside C (no triangle, no
+            // nonfinite row scale) rounds without per-element checks
+            const bool interior = fits && __all_sync(0xFFFFFFFFu, rowok && e_row != kNonFinite) &&
+                                  col0 + CPT <= a.N && !a.lower;
+            if (interior) {
+#pragma unroll
+              for (int c = 0; c < CPT; ++c, cp += a.ldc) {
+                const int f = __shfl_sync(0xFFFFFFFFu, fcol[0], c);
+                const double D = (f == kNonFinite) ? __longlong_as_double(0x7FF8000000000000ll)
+                                                   : rn_sum64((long long)R[c], e_row + f + sh0);
+                if (UPD == kSub)
+                  red_add_f64(cp, neg_d(D));
+                else if (UPD == kSet)
+                  *cp = D;
+                else
+                  *cp = apply_update<UPD>(a, D, needs_c ? *cp : 0.0);
+              }
+            } else
 #pragma unroll
             for (int c4 = 0; c4 < CPT / 4; ++c4) {
               uint32_t r[4] = {0u, 0u, 0u, 0u};
