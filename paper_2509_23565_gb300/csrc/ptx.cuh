@@ -179,9 +179,13 @@ __device__ __forceinline__ void tma_load_3d_pair_elect(void* dst, const CUtensor
       "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cl), "r"(c0), "r"(c1), "r"(c2)
       : "memory");
 }
-// Arrive on the barrier at shared::cluster address `bar_cl` (release at cluster scope).
+// Arrive on the barrier at shared::cluster address `bar_cl`, relaxed: it
+// orders nothing but itself.  The TMEM-slot release needs no more: the slot's
+// tcgen05.ld have completed (tcgen05.wait::ld) before it, and the global
+// updates of C the thread issued are not what the barrier protects (a release
+// at cluster scope would wait for every one of them to be performed).
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cl) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cl) : "memory");
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cl) : "memory");
 }
 // Bounded wait with acquire at cluster scope (arrivals from the other CTA), by
 // every lane of a warp; warp-uniform answer.
