@@ -36,10 +36,10 @@ METRIC_NOPIV = "emulated-FP64 LU without pivoting TFLOP/s on one GB300 at backwa
 METRIC_CHOL = "emulated-FP64 Cholesky TFLOP/s vs native-FP64 Cholesky on one GB300 at backward error ≤16"
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum (609.0 + 500.6 MB) of one launch of the
-# product kernel on 8192^2 x 256 at s = 7 (full ncu capture), over the algorithmic
+# dram__bytes_read.sum + dram__bytes_write.sum (623.6 + 488.2 MB) of one launch of the
+# product kernel (CTA pairs) on 8192^2 x 256 at s = 7 (full ncu capture), over the algorithmic
 # bytes of the same launch (C 8192^2 x 16 B + slices 2 x 7 x 8192 x 256 x 2 B)
-TRAFFIC_RATIO = (609.01e6 + 500.64e6) / (8192.0 * 8192.0 * 16.0 + 2 * 7 * 8192 * 256 * 2.0)
+TRAFFIC_RATIO = (623.625216e6 + 488.196608e6) / (8192.0 * 8192.0 * 16.0 + 2 * 7 * 8192 * 256 * 2.0)
 
 
 def lu_flops(n):

@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (PAIR)
         mbar_arrive_cluster(slot_empty0 + (uint32_t)(slot * 8));
       else
-        mbar_arrive(&slot_empty[slot]);
+        mbar_arrive_relaxed(&slot_empty[slot]);
     };
     for (int tile = cta0; tile < a.ntiles && ok; tile += ncta, ++tloc) {
       int tm, tn;
