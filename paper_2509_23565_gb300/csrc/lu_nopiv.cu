@@ -12,8 +12,8 @@
 //      halves' unit-lower inverses, X21 = -X22 (L21 X11);
 //   2. U12 = X A12 with X = L11^-1 of the whole block (emulated product);
 //   3. A22 <- A22 - L21 U12 (emulated product, alpha = -1, beta = 1).
-// The Schur updates and U12 run as products over K chunks of at most 256, so
-// every product keeps the 128-column tile (see gemm_kchunks).
+// The Schur updates and U12 run as products over K chunks of at most 1024, so
+// every product at s <= 7 keeps the 128-column tile (see gemm_kchunks).
 // No row is ever exchanged, so the factorization is stable only for matrices
 // that need no pivoting (diagonally dominant, SPD).
 #include <cuda_runtime.h>
@@ -27,7 +27,7 @@ constexpr int kNpLeaf = 64;           // widest diagonal block factored in one C
 constexpr int kNpThreads = 1024;      // 64 rows x 16 column groups
 constexpr int kNpGroups = kNpThreads / kNpLeaf;
 constexpr int kNpPerThread = kNpLeaf / kNpGroups;
-constexpr int kNpChunk = 256;         // K of one emulated product in the Schur updates
+constexpr int kNpChunk = 1024;        // K of one emulated product in the Schur updates
 constexpr size_t kNpAl = 256;
 
 inline size_t np_al(size_t x) { return (x + kNpAl - 1) / kNpAl * kNpAl; }
@@ -144,9 +144,10 @@ struct NpBufs {
 
 // C <- beta C + alpha A B as consecutive emulated products over K chunks of at
 // most kNpChunk (each rounded once; C must not overlap A or B).  A wider K
-// would need more than two accumulator jobs for the last level in the
-// 128-column product, which then falls back to 64-column tiles at half the
-// rate; C is read and written once per chunk instead.
+// would need level 2 in more than one accumulator job (1040 products of
+// 127^2 per FP32 accumulator), which the 128-column product cannot take: it
+// would fall back to 64-column tiles at half the rate; C is read and written
+// once per chunk instead.
 int gemm_kchunks(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Operand B, double beta, double* C,
                  long ldc, int s) {
   for (int c0 = 0; c0 < k; c0 += kNpChunk) {
