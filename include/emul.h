@@ -122,7 +122,7 @@ int emul_dgemm(emul_handle_t h, int m, int n, int k, double alpha, const double*
  * levels L = 2..threshold, threshold = 2s being the full s^2-pair product.
  * The result is D = RN(sum_{L<=t} I_L 2^(e + f - 7L)), exact sum, one rounding.
  * Returns EMUL_INVALID_ARG for a threshold outside that range and
- * EMUL_NOT_SUPPORTED when k is too large for the 128-bit Horner state at this
+ * EMUL_NOT_SUPPORTED when k is too large for the 128-bit exact sum at this
  * threshold (sum_L n_L 127^2 2^(7(t-L)) k >= 2^126). */
 int emul_dgemm_threshold(emul_handle_t h, int m, int n, int k, double alpha, const double* A, int lda,
                          const double* B, int ldb, double beta, double* C, int ldc, int slices, int threshold);

@@ -279,7 +279,7 @@ bool narrow_ok(int s, int k, int t = 0, int sa = 0, int sb = 0) {
   return r < 2305843009213693952.0L;   // 2^61
 }
 
-// The wide variant's complete 128-bit Horner state must stay below 2^126.
+// The wide variant's 128-bit exact sum T must stay below 2^126.
 bool wide_ok(int s, int t, int k, int sa = 0, int sb = 0) {
   const int nch = (k + kBK - 1) / kBK;
   return horner_bound_per_k(PairSet{sa ? sa : s, sb ? sb : s}, t) * static_cast<long double>(nch * kBK) < 8.5e37L;
@@ -462,7 +462,7 @@ int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Oper
   if (nit == h->narrow_cache.end()) nit = h->narrow_cache.emplace(nkey, narrow_ok(s, k, t, s_a, s_b)).first;
   const bool wide = !nit->second;
   if (wide && mode == 0 && !wide_ok(s, t, k, s_a, s_b))
-    return set_error(h, EMUL_NOT_SUPPORTED, "threshold too high for this k: the 128-bit Horner state could overflow");
+    return set_error(h, EMUL_NOT_SUPPORTED, "threshold too high for this k: the 128-bit exact sum could overflow");
   const int nch = (k + kBK - 1) / kBK;
   Sweep* sched = nullptr;
   int nsweeps = 0;

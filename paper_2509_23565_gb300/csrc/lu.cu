@@ -524,7 +524,7 @@ __global__ void __launch_bounds__(256) trsm_small_kernel(double* A, long lda, in
 }
 
 // ---------------------------------------------------------------- Cholesky diagonal block
-// The nb x nb diagonal block of a Cholesky step (nb <= 256) is factored in
+// The nb x nb diagonal block of a Cholesky step (nb <= 512) is factored in
 // FP64 by 32-column panels: a one-block leaf factors the panel's 32 x 32
 // diagonal block in shared memory, the rows below it within the block are
 // solved against it and the rest of the block is updated by a small FP64

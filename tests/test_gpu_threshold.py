@@ -4,7 +4,7 @@ parameter (Section 2, Eq. 2: the slice pairs kept are those with p + q <= t).
 emul_dgemm_threshold must equal the oracle's emul_gemm(..., t=t) bit for bit
 for thresholds below, at and above the method's t = s + 1, up to the full
 s^2-pair product t = 2s; t = s + 1 must reproduce emul_dgemm; a threshold
-outside 2..2s, or one whose 128-bit Horner state could overflow at this k, is
+outside 2..2s, or one whose 128-bit exact sum could overflow at this k, is
 refused on the host before any launch.
 """
 import numpy as np
@@ -103,7 +103,7 @@ def test_threshold_refused_on_host(gpu_lib):
     for s, t in ((4, 1), (4, 9), (7, 15)):
         with pytest.raises(EmulError, match="INVALID_ARG"):
             gpu_lib.dgemm(A, B, C, s, t=t)
-    # s = 8, t = 16: the Horner state grows by about 2^112 per unit of k, so
+    # s = 8, t = 16: the exact sum grows by about 2^112 per unit of k, so
     # k = 20000 could exceed 2^126 and is refused; k = 4096 is accepted
     A, B = ColMajor.empty(2, 20000), ColMajor.empty(20000, 2)
     with pytest.raises(EmulError, match="NOT_SUPPORTED"):
