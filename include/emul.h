@@ -193,13 +193,18 @@ int emul_autotune_nb(emul_handle_t h, int kind, int n, int slices, int* nb_out);
 int emul_dgetrf_nopiv(emul_handle_t h, int n, double* A, int lda, int nb, int slices, int32_t* info,
                       emul_stats* stats);
 
-/* Solve A X = B with the factors from emul_dgetrf: B (n x nrhs, ldb) is
- * overwritten by X.  FP64 substitution. */
+/* Solve A X = B with the factors from emul_dgetrf (Section 4, Eq. 5: the
+ * solution of A x = b through the triangular factors of the 2 x 2 blocked
+ * partition of Eq. 6): the row interchanges, then forward substitution with
+ * unit L and back substitution with U, in FP64.  B (n x nrhs, ldb) is
+ * overwritten by X. */
 int emul_dgetrs(emul_handle_t h, int n, int nrhs, const double* LU, int lda, const int32_t* ipiv, double* B,
                 int ldb);
 
 /* Lower Cholesky A = L L^T of the symmetric positive definite n x n matrix A
- * (lda), in place; only the lower triangle is read and written.  Block size
+ * (lda), in place; only the lower triangle is read and written.  Section 4
+ * notes that the method applies to symmetric positive definite matrices as
+ * well: the Schur complement of Eq. 7 becomes A22 - L21 L21^T.  Block size
  * nb (16..512, multiple of 16; 0 = default 128; EMUL_NB_AUTO = tuned by
  * emul_autotune_nb).  Diagonal blocks in FP64;
  * L21 = A21 L11^-T and the trailing update (lower tiles only) use the
@@ -207,7 +212,9 @@ int emul_dgetrs(emul_handle_t h, int n, int nrhs, const double* LU, int lda, con
 int emul_dpotrf(emul_handle_t h, char uplo, int n, double* A, int lda, int nb, int slices, int32_t* info,
                 emul_stats* stats);
 
-/* Solve A X = B from emul_dpotrf's factor (B n x nrhs, overwritten). */
+/* Solve A X = B from emul_dpotrf's factor (Section 4, Eq. 5, with A = L L^T):
+ * forward substitution with L, back substitution with L^T, in FP64.  B (n x
+ * nrhs, ldb) is overwritten by X. */
 int emul_dpotrs(emul_handle_t h, char uplo, int n, int nrhs, const double* L, int lda, double* B, int ldb);
 
 /* Residual measures of the solve (Section 4, Eq. 8), computed in FP64 on the
