@@ -349,67 +349,55 @@ __global__ void __launch_bounds__(kLeafThreads) getf2_leaf_kernel(double* A, lon
 
 // Row interchanges ipiv[k1..k2) (1-based global rows, ipiv[k]-1 >= k) resolved
 // into a gather map: after the interchanges, row dst[i] holds the original row
-// src[i], for the *count affected rows (at most 2 (k2-k1)).  Rows k < k2 are
-// final once interchange k is done, so one pass with a small hash of the rows
-// beyond the block suffices.  One thread.
+// src[i], for the *count affected rows (at most 2 (k2-k1)).  Applying
+// transposition k to every row in turn, the content ending at row r is
+// sigma(r) = t_k1(t_k1+1(... t_k2-1(r))): the transpositions taken in reverse
+// order on r alone, so every row is resolved by its own thread (thread i:
+// row k1+i, and row ipiv[k1+i]-1 when it lies beyond the block and no earlier
+// interchange names it).  The map's order is immaterial to its users.
 constexpr int kPermMax = 256;          // interchanges per gather map (longer ranges: several maps)
-constexpr int kHash = 1024;
-__global__ void laswp_perm_kernel(const int32_t* ipiv, int k1, int k2, int* map /* [2][2*kPermMax] + count */) {
-  __shared__ int cont[kPermMax];                 // content of rows k1..k2-1
-  __shared__ int hkey[kHash], hval[kHash];       // rows >= k2 that were touched
-  __shared__ int order[kPermMax];
+__global__ void __launch_bounds__(kPermMax) laswp_perm_kernel(const int32_t* ipiv, int k1, int k2,
+                                                             int* map /* [2][2*kPermMax] + count */) {
   __shared__ int piv_s[kPermMax];
+  __shared__ int cnt_s;
   const int nb = k2 - k1;
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-    cont[i] = k1 + i;
-    piv_s[i] = ipiv[k1 + i] - 1;
-  }
-  for (int i = threadIdx.x; i < kHash; i += blockDim.x) hkey[i] = -1;
+  const int i = threadIdx.x;
+  if (i < nb) piv_s[i] = ipiv[k1 + i] - 1;
+  if (i == 0) cnt_s = 0;
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  int nout = 0;
-  auto slot_of = [&](int row) {
-    int h = (row * 2654435761u) & (kHash - 1);
-    while (hkey[h] != -1 && hkey[h] != row) h = (h + 1) & (kHash - 1);
-    return h;
-  };
-  for (int k = k1; k < k2; ++k) {
-    const int p = piv_s[k - k1];
-    if (p == k) continue;
-    if (p < k2) {
-      const int t = cont[k - k1];
-      cont[k - k1] = cont[p - k1];
-      cont[p - k1] = t;
-    } else {
-      const int h = slot_of(p);
-      if (hkey[h] == -1) {
-        hkey[h] = p;
-        hval[h] = p;
-        order[nout++] = h;
-      }
-      const int t = cont[k - k1];
-      cont[k - k1] = hval[h];
-      hval[h] = t;
-    }
-  }
   int* dst = map;
   int* src = map + 2 * kPermMax;
-  int cnt = 0;
-  for (int i = 0; i < nb; ++i)
-    if (cont[i] != k1 + i) {
-      dst[cnt] = k1 + i;
-      src[cnt] = cont[i];
-      ++cnt;
+  auto sigma = [&](int r) {
+    for (int k = nb - 1; k >= 0; --k) {
+      const int p = piv_s[k], kk = k1 + k;
+      r = r == kk ? p : (r == p ? kk : r);
     }
-  for (int j = 0; j < nout; ++j) {
-    const int h = order[j];
-    if (hval[h] != hkey[h]) {
-      dst[cnt] = hkey[h];
-      src[cnt] = hval[h];
-      ++cnt;
+    return r;
+  };
+  if (i < nb) {
+    const int r = k1 + i;
+    const int sr = sigma(r);
+    if (sr != r) {
+      const int pos = atomicAdd(&cnt_s, 1);
+      dst[pos] = r;
+      src[pos] = sr;
+    }
+    const int p = piv_s[i];
+    if (p >= k2) {
+      bool first = true;
+      for (int j = 0; j < i && first; ++j) first = piv_s[j] != p;
+      if (first) {
+        const int sp = sigma(p);
+        if (sp != p) {
+          const int pos = atomicAdd(&cnt_s, 1);
+          dst[pos] = p;
+          src[pos] = sp;
+        }
+      }
     }
   }
-  map[4 * kPermMax] = cnt;
+  __syncthreads();
+  if (i == 0) map[4 * kPermMax] = cnt_s;
 }
 
 // Apply the gather map to columns [c0, c1): each block owns 8 columns, reads
@@ -1026,7 +1014,7 @@ int launch_leaf(emul_handle_t h, double* A, long lda, int n, int d0, int w, int 
 int laswp_prepare(emul_handle_t h, const int32_t* ipiv, int k1, int k2, int* map) {
   if (k2 <= k1) return EMUL_OK;
   if (k2 - k1 > kPermMax) return set_error(h, EMUL_INVALID_ARG, "too many interchanges in one block");
-  laswp_perm_kernel<<<1, 32, 0, h->stream>>>(ipiv, k1, k2, map);
+  laswp_perm_kernel<<<1, kPermMax, 0, h->stream>>>(ipiv, k1, k2, map);
   h->launches++;
   return check_cuda(h, cudaGetLastError(), "laswp map");
 }
@@ -1520,10 +1508,17 @@ int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int n
   int rc = emul::check_cuda(h, cudaMemsetAsync(info, 0, sizeof(int32_t), h->stream), "info reset");
   if (rc) return rc;
   const size_t gw = emul::gemm_workspace_bytes(n, n, nb, s_fixed, false);
-  // after the product and LU buffers: G, H (n ints each) and one panel of rows (n x nb doubles)
+  // after the product and LU buffers: G, H (n ints each), one panel of rows
+  // (n x nb doubles) and every panel's gather maps (kept from the loop for the
+  // deferred interchanges of the L columns)
+  const int npanel = (n + nb - 1) / nb;
+  const int cpp = (nb + emul::kPermMax - 1) / emul::kPermMax;   // gather maps per panel
   const size_t def_off = emul::al(emul::al(gw) + emul::lu_extra_bytes(nb, h->nsm));
-  rc = emul::reserve_workspace(h, def_off + emul::al(8ull * n) + emul::al(8ull * n * nb));
+  const size_t maps_off = def_off + emul::al(8ull * n) + emul::al(8ull * n * nb);
+  rc = emul::reserve_workspace(
+      h, maps_off + emul::al(static_cast<size_t>(npanel) * cpp * emul::kMapInts * sizeof(int)));
   if (rc) return rc;
+  int* maps = reinterpret_cast<int*>(static_cast<uint8_t*>(h->ws) + maps_off);
   const emul::LuBufs B = emul::carve(h, gw, nb);
   rc = emul::check_cuda(h, cudaMemsetAsync(B.recs, 0, emul::rec_bytes(h->nsm), h->stream), "leaf records");
   if (rc) return rc;
@@ -1537,8 +1532,15 @@ int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int n
     emul::phase_end(h, ph);
     if (rc) return rc;
     ph = emul::phase_begin(h, EMUL_PHASE_SWAP);
-    // the columns left of the panel get all later interchanges at once, after the loop
-    rc = emul::laswp(h, A, lda, j0 + jb, n, ipiv, j0, j0 + jb, B.map);
+    // the columns right of the panel; the columns left of it get all later
+    // interchanges at once, after the loop, from the same maps
+    for (int c = 0; c < cpp && !rc; ++c) {
+      const int k1 = j0 + c * emul::kPermMax, k2 = k1 + emul::kPermMax < j0 + jb ? k1 + emul::kPermMax : j0 + jb;
+      if (k1 >= k2) break;
+      int* map = maps + static_cast<size_t>(j0 / nb * cpp + c) * emul::kMapInts;
+      rc = emul::laswp_prepare(h, ipiv, k1, k2, map);
+      if (!rc) rc = emul::laswp_apply(h, A, lda, j0 + jb, n, map);
+    }
     emul::phase_end(h, ph);
     if (rc) return rc;
     const int m2 = n - j0 - jb;
@@ -1641,10 +1643,9 @@ int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int n
     for (int k = K - 2; k >= 0; --k) {
       const int r0 = (k + 1) * nb, r1 = r0 + nb < n ? r0 + nb : n;
       // panel k+1's interchanges, composed from its last gather map back
-      for (int q0 = r0 + (r1 - r0 - 1) / emul::kPermMax * emul::kPermMax; q0 >= r0; q0 -= emul::kPermMax) {
-        rc = emul::laswp_prepare(h, ipiv, q0, q0 + emul::kPermMax < r1 ? q0 + emul::kPermMax : r1, B.map);
-        if (rc) return rc;
-        emul::compose_kernel<<<1, 512, 0, h->stream>>>(B.map, G, H);
+      for (int c = (r1 - r0 - 1) / emul::kPermMax; c >= 0; --c) {
+        emul::compose_kernel<<<1, 512, 0, h->stream>>>(maps + static_cast<size_t>((k + 1) * cpp + c) * emul::kMapInts,
+                                                       G, H);
         h->launches++;
       }
       emul::gather_rows_kernel<<<dim3((n - r0 + 255) / 256, nb), 256, 0, h->stream>>>(A, lda, r0, n, k * nb, G,
