@@ -627,6 +627,12 @@ int emul_destroy(emul_handle_t h) {
     cudaEventDestroy(r.e1);
   }
   for (auto ev : h->event_pool) cudaEventDestroy(ev);
+  if (h->aux) {
+    cudaStreamSynchronize(h->aux);
+    cudaStreamDestroy(h->aux);
+  }
+  if (h->aux_start) cudaEventDestroy(h->aux_start);
+  if (h->aux_done) cudaEventDestroy(h->aux_done);
   emul::selector_free(h);
   emul::batched_free(h);
   if (h->ws) cudaFree(h->ws);

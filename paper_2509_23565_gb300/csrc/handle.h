@@ -45,6 +45,10 @@ struct emul_handle_s {
   std::vector<PhaseRec> phases;
   std::vector<cudaEvent_t> event_pool;
   std::map<uint64_t, int> nb_tuned;  // (kind, n, slices) -> block size chosen by emul_autotune_nb
+  // second stream of the LU step: L11^-1 is formed there while the row
+  // interchanges run on `stream` (created on first use, same device)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t aux_start = nullptr, aux_done = nullptr;
   void* selector = nullptr;         // emul::SelectorState (selector.cu)
   void* batched = nullptr;          // emul::BatchedState (batched.cu)
 };

@@ -1414,6 +1414,15 @@ uint64_t nb_key(int kind, int n, int slices) {
   return (static_cast<uint64_t>(kind) << 40) | (static_cast<uint64_t>(slices) << 32) | static_cast<uint32_t>(n);
 }
 
+// The LU step's second stream and its two events, created on first use.
+int aux_ready(emul_handle_t h) {
+  if (h->aux) return EMUL_OK;
+  int rc = check_cuda(h, cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking), "second stream");
+  if (!rc) rc = check_cuda(h, cudaEventCreateWithFlags(&h->aux_start, cudaEventDisableTiming), "stream events");
+  if (!rc) rc = check_cuda(h, cudaEventCreateWithFlags(&h->aux_done, cudaEventDisableTiming), "stream events");
+  return rc;
+}
+
 // nb = EMUL_NB_AUTO: the tuned block size for (kind, n, slices), tuning first
 // when there is none.
 int resolve_nb(emul_handle_t h, int kind, int n, int slices, int* nb) {
@@ -1531,6 +1540,23 @@ int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int n
     rc = emul::panel_getrf(h, A, lda, n, j0, jb, ipiv, info, autos ? s_prev : s_fixed, B);
     emul::phase_end(h, ph);
     if (rc) return rc;
+    const int m2 = n - j0 - jb;
+    // L11^-1 on the second stream (L11 is final: the leaves interchanged the
+    // panel's own rows) while the interchanges reach the columns right of it
+    bool joined = true;
+    if (m2 > 0) {
+      rc = emul::aux_ready(h);
+      if (!rc) rc = emul::check_cuda(h, cudaEventRecord(h->aux_start, h->stream), "stream events");
+      if (!rc) rc = emul::check_cuda(h, cudaStreamWaitEvent(h->aux, h->aux_start, 0), "stream events");
+      if (rc) return rc;
+      emul::trtri_cols_kernel<<<(jb + 1) / 2, emul::trtri_threads(jb), 0, h->aux>>>(A, lda, j0, jb, 1, B.inv,
+                                                                                       nullptr);
+      h->launches++;
+      rc = emul::check_cuda(h, cudaGetLastError(), "trtri");
+      if (!rc) rc = emul::check_cuda(h, cudaEventRecord(h->aux_done, h->aux), "stream events");
+      if (rc) return rc;
+      joined = false;
+    }
     ph = emul::phase_begin(h, EMUL_PHASE_SWAP);
     // the columns right of the panel; the columns left of it get all later
     // interchanges at once, after the loop, from the same maps
@@ -1542,15 +1568,14 @@ int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int n
       if (!rc) rc = emul::laswp_apply(h, A, lda, j0 + jb, n, map);
     }
     emul::phase_end(h, ph);
+    // the stream waits for L11^-1 on every path, so no work of this call is left behind on the second stream
+    if (!joined) {
+      const int rj = emul::check_cuda(h, cudaStreamWaitEvent(h->stream, h->aux_done, 0), "stream events");
+      if (!rc) rc = rj;
+    }
     if (rc) return rc;
-    const int m2 = n - j0 - jb;
     if (m2 > 0) {
       ph = emul::phase_begin(h, EMUL_PHASE_U12);
-      emul::trtri_cols_kernel<<<(jb + 1) / 2, emul::trtri_threads(jb), 0, h->stream>>>(A, lda, j0, jb, 1, B.inv,
-                                                                                          nullptr);
-      h->launches++;
-      rc = emul::check_cuda(h, cudaGetLastError(), "trtri");
-      if (rc) return rc;
       double* A12 = A + j0 + static_cast<long>(j0 + jb) * lda;
       // U12 = L11^-1 A12 (jb x m2), written over A12
       rc = emul::gemm_run(h, jb, m2, jb, 1.0, Operand{B.inv, 1, jb}, Operand{A12, lda, 1}, 0.0, A12, lda,
