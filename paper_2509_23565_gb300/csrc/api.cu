@@ -472,7 +472,12 @@ int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Oper
   const int BN = wide ? 64 : 128;
   // CTA pairs (cta_group::2) for the 128-column tile once there are two
   // 128-row tiles: each SM stages half of B, a quarter less than alone
-  const bool pair = !wide && m > 128 && h->nsm >= 2;
+  bool pair = !wide && m > 128 && h->nsm >= 2;
+  if (pair) {
+    size_t smem_pair = 0;
+    gemm_stages(false, s, true, &smem_pair);
+    pair = gemm_pair_capacity(smem_pair) >= 1;   // else one CTA per tile
+  }
   CUtensorMap tmA, tmB;
   rc = encode_slices_map(h, &tmA, sa, m, k, kp, s, 128);
   if (rc) return rc;
@@ -511,12 +516,9 @@ int gemm_run(emul_handle_t h, int m, int n, int k, double alpha, Operand A, Oper
   a.status = h->d_status;
   a.wait_limit = h->wait_limit;
 
-  const size_t stage = gemm_stage_bytes(wide, s, pair);
-  const size_t budget = 232448 - 1024 - 2048;
-  int stages = static_cast<int>(budget / stage);
-  if (stages > kMaxStagesCfg) stages = kMaxStagesCfg;
+  size_t smem = 0;
+  const int stages = gemm_stages(wide, s, pair, &smem);
   if (stages < 2) return set_error(h, EMUL_NOT_SUPPORTED, "slice tiles do not fit in shared memory");
-  const size_t smem = stages * stage + 1024;
   const int units = pair ? h->nsm / 2 : h->nsm;   // CTAs, or CTA pairs
   const int grid = (a.ntiles < units ? a.ntiles : units) * (pair ? 2 : 1);
   emul_handle_s::ProfRec rec{};

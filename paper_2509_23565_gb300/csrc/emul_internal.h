@@ -67,5 +67,9 @@ cudaError_t launch_split(cudaStream_t st, int rows, int k, const double* X, long
 cudaError_t launch_gemm(cudaStream_t st, bool wide, bool pair, const CUtensorMap& tmA, const CUtensorMap& tmB,
                         const GemmArgs& args, int grid, int stages, size_t smem_bytes);
 size_t gemm_stage_bytes(bool wide, int s, bool pair);
+// Ring stages of a launch and its shared-memory bytes.
+int gemm_stages(bool wide, int s, bool pair, size_t* smem_bytes);
+// CTA pairs that can be resident at once with this much shared memory.
+int gemm_pair_capacity(size_t smem_bytes);
 
 }  // namespace emul

@@ -626,6 +626,47 @@ size_t gemm_stage_bytes(bool wide, int s, bool pair) {
               : (size_t)s * (Cfg<false>::A_TILE + (pair ? Cfg<false>::B_TILE / 2 : Cfg<false>::B_TILE));
 }
 
+// Ring stages and shared-memory bytes of a launch.
+int gemm_stages(bool wide, int s, bool pair, size_t* smem_bytes) {
+  const size_t stage = gemm_stage_bytes(wide, s, pair);
+  int stages = static_cast<int>((232448 - 1024 - 2048) / stage);
+  if (stages > kMaxStagesCfg) stages = kMaxStagesCfg;
+  if (smem_bytes) *smem_bytes = stages * stage + 1024;
+  return stages;
+}
+
+// CTA pairs of the product kernel that can be resident at once with this much
+// shared memory (0: none, e.g. on a partition without two free SMs side by side).
+int gemm_pair_capacity(size_t smem_bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, size_t>, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_pair(dev, smem_bytes);
+  const auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  auto kern = gemm_kernel<false, kSub, true>;
+  int pairs = 0;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem_bytes;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaOccupancyMaxActiveClusters(&pairs, kern, &cfg) != cudaSuccess) pairs = 0;
+  }
+  cudaGetLastError();   // a failed query leaves no error behind
+  cache[key] = pairs;
+  return pairs;
+}
+
 template <bool WIDE, int UPD, bool PAIR>
 cudaError_t launch_one(cudaStream_t st, const CUtensorMap& tmA, const CUtensorMap& tmB, const GemmArgs& args, int grid,
                        int stages, size_t smem_bytes) {
@@ -656,24 +697,7 @@ cudaError_t launch_one(cudaStream_t st, const CUtensorMap& tmA, const CUtensorMa
   cfg.numAttrs = 1;
   // the persistent grid holds no more pairs than can be resident at once (an
   // SM left without a partner would otherwise run its pair after the others)
-  static std::mutex mu;
-  static std::map<std::pair<int, size_t>, int> resident;   // (device, shared memory) -> pairs
-  int dev = 0;
-  e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  int pairs = 0;
-  {
-    std::lock_guard<std::mutex> lock(mu);
-    const auto key = std::make_pair(dev, smem_bytes);
-    const auto it = resident.find(key);
-    if (it != resident.end()) {
-      pairs = it->second;
-    } else {
-      e = cudaOccupancyMaxActiveClusters(&pairs, kern, &cfg);
-      if (e != cudaSuccess) return e;
-      resident[key] = pairs;
-    }
-  }
+  const int pairs = gemm_pair_capacity(smem_bytes);
   if (pairs < 1) return cudaErrorInvalidConfiguration;
   if (grid > 2 * pairs) cfg.gridDim = dim3(2 * pairs);
   return cudaLaunchKernelEx(&cfg, kern, tmA, tmB, args, stages);

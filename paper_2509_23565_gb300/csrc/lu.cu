@@ -1501,6 +1501,7 @@ int emul_dgetrf(emul_handle_t h, int n, double* A, int lda, int32_t* ipiv, int n
     const int rc = emul::resolve_nb(h, 0, n, slices, &nb);
     if (rc) return rc;
   }
+  if (nb == EMUL_NB_AUTO && n == 0) nb = 128;
   if (nb == 0) nb = 128;
   if (n < 0 || lda < (n > 1 ? n : 1) || nb < 16 || nb > 512 || nb % 16 != 0 || slices < 0 ||
       slices > emul::kMaxSlices || (n > 0 && (!A || !ipiv || !info)))
@@ -1708,6 +1709,7 @@ int emul_dpotrf(emul_handle_t h, char uplo, int n, double* A, int lda, int nb, i
     const int rc = emul::resolve_nb(h, 1, n, slices, &nb);
     if (rc) return rc;
   }
+  if (nb == EMUL_NB_AUTO && n == 0) nb = 128;
   if (nb == 0) nb = 128;
   if ((uplo != 'L' && uplo != 'l') || n < 0 || lda < (n > 1 ? n : 1) || nb < 16 || nb > 512 || nb % 16 != 0 ||
       slices < 1 || slices > emul::kMaxSlices || (n > 0 && (!A || !info)))
