@@ -30,6 +30,12 @@
 // of one or two jobs shares the staged tiles of a chunk; each job's TMEM slot
 // (and the parity of its barriers) comes from a host-planned slot table, so the
 // issuer fills slots while the epilogue drains others.  All waits are bounded.
+//
+// With more than 128 rows the blocks run as CTA pairs (clusters of two,
+// cta_group::2, the PAIR instantiation): a pair owns a 256 x BN tile, each CTA
+// stages its 128 rows of A and half of B's rows, rank 0 issues M = 256 MMAs
+// that read both CTAs' tiles, and its commits reach the barriers of both; each
+// CTA drains its own TMEM.  Each SM then stages a quarter fewer bytes.
 #include <cstdint>
 #include <map>
 #include <mutex>
