@@ -152,6 +152,39 @@ def test_multiple_rhs(gpu_lib):
         assert residual.backward_error(A, X[:, j], B[:, j]) < 16
 
 
+@pytest.mark.parametrize("n,nrhs", [(700, 3), (1, 2), (257, 1), (600, 2)])
+def test_interchanges_exact(gpu_lib, n, nrhs):
+    """With unit factors (LU = I) the solve returns P B: the row interchanges
+    alone, applied from gather maps of at most 256 interchanges each (several
+    maps per call here) or, for one right-hand side, from the composite
+    permutation.  Pivot rows repeat, fall inside and beyond each map's rows,
+    and stay in place; the result must equal the interchanges applied one by
+    one, bit for bit."""
+    import torch
+    rng = np.random.default_rng(70 + n)
+    piv = np.empty(n, dtype=np.int32)
+    hot = rng.integers(0, n, 4)                  # rows named by many interchanges
+    for k in range(n):
+        u = rng.random()
+        if u < 0.2:
+            p = k
+        elif u < 0.5:
+            p = max(k, int(hot[rng.integers(0, 4)]))
+        else:
+            p = int(rng.integers(k, n))
+        piv[k] = p + 1
+    B = inputs.uniform(n, nrhs, seed=71 + n)
+    want = B.copy()
+    for k in range(n):
+        p = piv[k] - 1
+        want[[k, p]] = want[[p, k]]
+    dLU = ColMajor.from_numpy(np.eye(n))
+    dB = ColMajor.from_numpy(B, ld=n + 1)
+    gpu_lib.dgetrs(dLU, torch.from_numpy(piv).cuda(), dB)
+    gpu_lib.sync_status()
+    assert np.array_equal(dB.numpy(), want)
+
+
 @pytest.mark.parametrize("n,nb,cond", [(130, 32, 1e2), (512, 64, 1e8), (1000, 128, 1e12), (1000, 256, 1e8),
                                        (333, 48, 1e4), (1100, 512, 1e8), (700, 320, 1e12)])
 @pytest.mark.parametrize("s", [7, 8])
