@@ -521,75 +521,103 @@ __global__ void __launch_bounds__(256) trsm_small_kernel(double* A, long lda, in
 // keeps a large amount of FP64 work on a single SM.
 constexpr int kCholLeaf = 32;
 
-// Unblocked lower Cholesky of the w x w (w <= 32) block at A[d0.., d0..] in
-// shared memory, right-looking, one thread per entry (1024 threads): the pivot
-// d gives r = rsqrt(d), L_jj = d r, the column is scaled by r, then the
-// trailing lower triangle gets its rank-1 update.  GB300's FP64 latency makes
-// every dependent FP64 step costly, so each pivot takes one reciprocal square
-// root rather than a square root and a division.  A non-positive pivot sets
-// *info (first index) and stops; nothing runs once *info is set.
-// It also writes the leaf's inverse L^-1 (lower, w x w) to inv[i + j*ldi],
-// formed by recursive doubling: the diagonal reciprocals, then for h = 1, 2,
-// 4, 8, 16 every pair of h x h diagonal blocks is joined,
-// X21 = -X22 (L21 X11), so the dependent chains are short dot products.
-__global__ void __launch_bounds__(1024) chol_leaf_kernel(double* A, long lda, int d0, int w, double* inv, int ldi,
-                                                        int32_t* info) {
-  __shared__ double D[kCholLeaf][kCholLeaf + 1], X[kCholLeaf][kCholLeaf + 1], T[kCholLeaf][kCholLeaf + 1];
-  __shared__ double rj;
-  __shared__ int fail;
-  const int t = threadIdx.x, i = t & 31, j = t >> 5;
-  if (t == 0) fail = (*info != 0);
+// Unblocked lower Cholesky of the w x w (w <= 32) block at A[d0.., d0..],
+// right-looking, by four warps: lane i holds row i, warp q the columns
+// j = 4s + q (s = 0..7) in registers, so the FP64 work is spread over the
+// SM's four sub-partitions.  Pivot jj: its owner warp takes r = rsqrt(d) of
+// the pivot d, sets L_jj = d r, scales the column by r and publishes it in
+// shared memory (double-buffered, one 128-thread barrier per pivot); every
+// warp then updates its columns right of jj.  GB300's FP64 latency makes every
+// dependent FP64 step costly, so each pivot takes one reciprocal square root
+// rather than a square root and a division.  A non-positive pivot sets *info
+// (first index) and stops; nothing runs once *info is set.
+// It also writes the leaf's inverse L^-1 (lower, w x w) to inv[i + j*ldi]:
+// forward substitution on the identity, all columns at once, each warp on its
+// own columns (row m of X, once final, is broadcast within the warp by
+// shuffles; the multipliers L[i][m] come from shared memory), with the
+// diagonal reciprocals formed in parallel up front.
+__global__ void __launch_bounds__(128) chol_leaf_kernel(double* A, long lda, int d0, int w, double* inv, int ldi,
+                                                       int32_t* info) {
+  __shared__ double col[2][kCholLeaf];
+  __shared__ double Ls[kCholLeaf][kCholLeaf + 1];
+  __shared__ int fail_s;
+  const int i = threadIdx.x & 31, q = threadIdx.x >> 5;
+  if (threadIdx.x == 0) fail_s = (*info != 0);
   __syncthreads();
-  if (fail) return;
+  if (fail_s) return;
   double* blk = A + d0 + static_cast<long>(d0) * lda;
   // padding beyond w is the identity, so the inverse below needs no special case
-  D[i][j] = (i < w && j < w) ? (i >= j ? blk[i + static_cast<long>(j) * lda] : 0.0) : (i == j ? 1.0 : 0.0);
-  __syncthreads();
+  double d[8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int j = 4 * s + q;
+    d[s] = (i < w && j < w) ? (i >= j ? blk[i + static_cast<long>(j) * lda] : 0.0) : (i == j ? 1.0 : 0.0);
+  }
   int done = w;
-  for (int jj = 0; jj < w; ++jj) {
-    if (t == 0) {
-      const double d = D[jj][jj];
-      if (!(d > 0.0)) {
+#pragma unroll
+  for (int jj = 0; jj < kCholLeaf; ++jj) {
+    if (jj >= w) break;                       // uniform over the block
+    const int s0 = jj >> 2;
+    if (q == (jj & 3)) {
+      const double diag = __shfl_sync(0xFFFFFFFFu, d[s0], jj);
+      const bool ok = diag > 0.0;
+      if (ok) {
+        const double r = rsqrt(diag);
+        if (i == jj)
+          d[s0] = diag * r;
+        else if (i > jj)
+          d[s0] *= r;
+      } else if (i == 0) {
         atomicCAS(info, 0, d0 + jj + 1);
-        fail = 1;
-      } else {
-        const double r = rsqrt(d);
-        D[jj][jj] = d * r;
-        rj = r;
+        fail_s = 1;
       }
+      col[jj & 1][i] = i >= jj ? d[s0] : 0.0;
     }
-    __syncthreads();
-    if (fail) {
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    if (fail_s) {
       done = jj;
       break;
     }
-    if (j == jj && i > jj && i < w) D[i][jj] *= rj;
-    __syncthreads();
-    if (i > jj && j > jj && j <= i && i < w) D[i][j] = fma(-D[i][jj], D[j][jj], D[i][j]);
-    __syncthreads();
+    const double lij = col[jj & 1][i];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int j = 4 * s + q;
+      if (j > jj && i >= j) d[s] = fma(-lij, col[jj & 1][j], d[s]);
+    }
   }
   // write back the columns that were finished (all of them unless a pivot failed)
-  if (i < w && j < done && i >= j) blk[i + static_cast<long>(j) * lda] = D[i][j];
-  if (done < w) return;
-  X[i][j] = (i == j) ? 1.0 / D[i][i] : 0.0;
-  __syncthreads();
-  for (int h = 1; h < kCholLeaf; h <<= 1) {
-    const int o = (i / (2 * h)) * (2 * h);
-    const bool in21 = (j / (2 * h) == i / (2 * h)) && (i - o >= h) && (j - o < h);
-    if (in21) {   // T21 = L21 X11
-      double acc = 0.0;
-      for (int k = j; k < o + h; ++k) acc = fma(D[i][k], X[k][j], acc);
-      T[i][j] = acc;
-    }
-    __syncthreads();
-    if (in21) {   // X21 = -X22 T21
-      double acc = 0.0;
-      for (int k = o + h; k <= i; ++k) acc = fma(X[i][k], T[k][j], acc);
-      X[i][j] = -acc;
-    }
-    __syncthreads();
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int j = 4 * s + q;
+    if (i < w && j < done && i >= j) blk[i + static_cast<long>(j) * lda] = d[s];
   }
-  if (i < w && j < w) inv[i + static_cast<long>(j) * ldi] = X[i][j];
+  if (done < w) return;
+  // the factor in shared memory for the inverse's multipliers
+#pragma unroll
+  for (int s = 0; s < 8; ++s) Ls[i][4 * s + q] = d[s];
+  __syncthreads();
+  const double rcp = 1.0 / Ls[i][i];
+  double x[8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) x[s] = (i == 4 * s + q) ? 1.0 : 0.0;
+#pragma unroll
+  for (int m = 0; m < kCholLeaf; ++m) {
+    if (i == m) {
+#pragma unroll
+      for (int s = 0; s < 8; ++s) x[s] *= rcp;   // row m of X is final
+    }
+    const double lim = i > m ? Ls[i][m] : 0.0;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const double xm = __shfl_sync(0xFFFFFFFFu, x[s], m);
+      x[s] = fma(-lim, xm, x[s]);
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int j = 4 * s + q;
+    if (i < w && j < w) inv[i + static_cast<long>(j) * ldi] = x[s];
+  }
 }
 
 // C(i, j) = beta C(i, j) + alpha sum_l A(i, l) B(j, l) in FP64, for the m x n
@@ -939,7 +967,7 @@ size_t lu_extra_bytes(int nb, int nsm) {
 int chol_diag(emul_handle_t h, double* A, long lda, int d0, int jb, double* inv, int32_t* info, bool want_inv) {
   for (int c0 = 0; c0 < jb; c0 += kCholLeaf) {
     const int wp = kCholLeaf < jb - c0 ? kCholLeaf : jb - c0;
-    chol_leaf_kernel<<<1, 1024, 0, h->stream>>>(A, lda, d0 + c0, wp, inv + c0 + static_cast<long>(c0) * jb, jb,
+    chol_leaf_kernel<<<1, 128, 0, h->stream>>>(A, lda, d0 + c0, wp, inv + c0 + static_cast<long>(c0) * jb, jb,
                                                 info);
     h->launches++;
     const int r0 = c0 + wp, mr = jb - r0;
