@@ -37,7 +37,7 @@ struct PairSet {
 // Sum over the levels L = 2..last of n_L 2^(7(last-L)) times 127^2: the
 // worst-case magnitude per unit of k of T = sum_L I_L 2^(7(last-L)) (the
 // wide variant's state after all its jobs, last = t).
-long double horner_bound_per_k(const PairSet& ps, int last) {
+long double exact_sum_bound_per_k(const PairSet& ps, int last) {
   long double acc = 0.0L;
   for (int L = 2; L <= last; ++L) acc = acc * 128.0L + ps.count(L);
   return acc * 127.0L * 127.0L;
@@ -282,7 +282,7 @@ bool narrow_ok(int s, int k, int t = 0, int sa = 0, int sb = 0) {
 // The wide variant's 128-bit exact sum T must stay below 2^126.
 bool wide_ok(int s, int t, int k, int sa = 0, int sb = 0) {
   const int nch = (k + kBK - 1) / kBK;
-  return horner_bound_per_k(PairSet{sa ? sa : s, sb ? sb : s}, t) * static_cast<long double>(nch * kBK) < 8.5e37L;
+  return exact_sum_bound_per_k(PairSet{sa ? sa : s, sb ? sb : s}, t) * static_cast<long double>(nch * kBK) < 8.5e37L;
 }
 
 // Device copy of a schedule: the sweeps, then the slot table (16-byte aligned).
