@@ -168,6 +168,20 @@ def test_lu_schedule_shape():
     assert info["njobs"] == 11
 
 
+def test_narrow_reach_at_s7():
+    """At s = 7 the 128-column variant schedules every k up to 1024 (32 chunks):
+    level 2, one pair, fits the exactness budget over 1024 in one job, which
+    the final job must be; at 1056 it would need two, so only the wide variant
+    schedules it."""
+    for k in (32, 256, 512, 1000, 1024):
+        r = binding.schedule(7, k)
+        assert r is not None, k
+        last = r[0][-1]
+        assert (last["L0"], last["L1"], last["flags0"]) == (2, 0, FINAL) and last["k1c"] - last["k0c"] == (k + 31) // 32
+    assert binding.schedule(7, 1056) is None
+    assert binding.schedule(7, 1056, wide=True) is not None
+
+
 @pytest.mark.parametrize("s", [1, 4, 7])
 def test_threshold_out_of_range(s):
     for t in (1, 2 * s + 1):
